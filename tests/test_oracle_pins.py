@@ -119,6 +119,11 @@ def test_warp_nonfinite_and_huge_give_zero():
         M = np.array(M, np.float32)
         np.testing.assert_array_equal(oracle.warp_u8(img, M, 4, 4), 0)
         np.testing.assert_array_equal(oracle.warp_f64(img, M, 4, 4), 0.0)
+        assert not oracle.warp_point(M, 1, 1)[0]
+    # The range limit is |s| < 2^22 on each axis separately.
+    assert oracle.warp_point(np.array([[0, 0, 4194303.5], [0, 0, 0.5]], np.float32), 0, 0)[0]
+    assert not oracle.warp_point(np.array([[0, 0, 0.5], [0, 0, 4194304.5]], np.float32), 0, 0)[0]
+    assert not oracle.warp_point(np.array([[0, 0, 0.5], [0, 0, -4194303.5]], np.float32), 0, 0)[0]
 
 
 def test_gray_all_rgb_within_bound():
