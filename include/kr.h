@@ -1,0 +1,223 @@
+/*
+ * kr.h -- C ABI of the GB300 (sm_103a) image-resampling library.
+ *
+ * Operators: bilinear resize and affine warp of HWC u8 images, each with an
+ * optional fused RGB -> gray and u8 -> f32 normalisation, a standalone
+ * RGB -> gray, a ragged batch of such operations in one persistent launch,
+ * and a continuous-batching serving loop built on the batch launch.
+ *
+ * Paper: Kornia-rs (arXiv 2505.12425). Sec. III names the image
+ * transformations this library computes (horizontal flip, oversizing,
+ * downsizing, RGB to grayscale); Sec. II-A places geometric transforms in
+ * kornia-imgproc; Sec. II-B fixes the calling conventions followed here:
+ * typed images Image<T, C> (element type + channel count), zero-copy views,
+ * caller-owned pre-allocated output buffers and no hidden allocation, and
+ * fallible calls that return an error instead of failing silently.
+ *
+ * Arithmetic (the paper prints none; these are the library's definitions):
+ *   resize   sx = (x + 1/2) W / w - 1/2, clamp to the edge;
+ *   warp     sx = fmaf(m00, x + 1/2, fmaf(m01, y + 1/2, m02)) - 1/2 (fp32,
+ *            round to nearest even), sy likewise with m10, m11, m12; M maps
+ *            destination pixels to source pixels; a tap outside the image
+ *            reads 0; |sx| or |sy| >= 2^22 (or NaN) gives a 0 sample;
+ *   u8       11-bit weights rounded half up, out = (v + 2^21) >> 22, exact;
+ *   f32      value p/255 interpolated with fp32 weights, then
+ *            (v - mean[c]) / std[c]; within 1e-5 of the exact result;
+ *   gray     u8: (4899 R + 9617 G + 1868 B + 8192) >> 14 of the rounded u8
+ *            interpolants; f32: 0.299 R + 0.587 G + 0.114 B of the f32
+ *            interpolants, normalised with mean[0], std[0].
+ *
+ * Memory and streams. Every image pointer is a DEVICE address owned by the
+ * caller; the library never allocates, frees or retains image memory. All
+ * work is enqueued asynchronously on the given stream (NULL = the legacy
+ * default stream) and the call returns at once; results are visible after
+ * the stream is synchronised. Source and destination must not overlap.
+ *
+ * Errors. Every argument is validated on the host before anything is
+ * enqueued; on a validation error nothing is enqueued and the status says
+ * why. KR_ERR_CUDA reports a failed launch or CUDA runtime call; the text of
+ * the last such error is returned by kr_last_error(). No call aborts,
+ * traps or throws across the ABI.
+ */
+#ifndef KR_H
+#define KR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (cudaStream_t / CUstream); NULL means the legacy default stream. */
+typedef struct CUstream_st *kr_stream_t;
+
+typedef enum { KR_U8 = 0, KR_F32 = 1 } kr_dtype;
+typedef enum { KR_HWC = 0, KR_CHW = 1 } kr_layout;
+
+typedef enum {
+    KR_OK = 0,
+    KR_ERR_INVALID_ARG = 1,   /* null pointer, bad size, pitch, dtype, layout or matrix */
+    KR_ERR_UNSUPPORTED = 2,   /* a valid combination this library does not implement   */
+    KR_ERR_ALIAS = 3,         /* source and destination memory overlap                 */
+    KR_ERR_CUDA = 4,          /* a CUDA launch or runtime call failed                  */
+    KR_ERR_NO_SPACE = 5,      /* workspace too small / request over the memory budget  */
+    KR_ERR_TIMEOUT = 6        /* a bounded wait ran out                                */
+} kr_status;
+
+/*
+ * An image, or a batch of equally sized images, in device memory
+ * (Sec. II-B: Image<T, C> with zero-copy views).
+ *
+ *   data          address of channel 0 of pixel (0, 0) of image 0;
+ *   height, width rows and columns, each >= 1;
+ *   channels      1 or 3 (RGB order for 3);
+ *   dtype         KR_U8 or KR_F32 (f32 only as a destination);
+ *   layout        KR_HWC: pixel (y, x) channel c at data + y*pitch + (x*C + c)*esize;
+ *                 KR_CHW (f32 destinations only): at data + c*plane_stride + y*pitch + x*4;
+ *   batch         number of images (>= 1); image n starts at data + n*batch_stride;
+ *   pitch         bytes between rows, >= width*C*esize (HWC) or width*4 (CHW);
+ *   plane_stride  bytes between channel planes (CHW; ignored for HWC);
+ *   batch_stride  bytes between images (ignored when batch == 1).
+ * A sub-rectangle of a larger image is described by moving `data` and keeping
+ * the parent's pitch. f32 images need 4-byte aligned data and strides.
+ */
+typedef struct {
+    void *data;
+    int32_t height;
+    int32_t width;
+    int32_t channels;
+    int32_t dtype;
+    int32_t layout;
+    int32_t batch;
+    int64_t pitch;
+    int64_t plane_stride;
+    int64_t batch_stride;
+} kr_image_t;
+
+/* Fused epilogue flags. */
+#define KR_GRAY      1u   /* 3-channel source -> 1-channel destination (BT.601)          */
+#define KR_NORMALIZE 2u   /* f32 destination: (v - mean[c]) / std[c]; needs dtype KR_F32 */
+
+/*
+ * Fused epilogue (Sec. III: RGB to grayscale; u8 -> f32 normalisation).
+ * NULL means "none". An f32 destination without KR_NORMALIZE stores v = p/255
+ * (mean 0, std 1). std[c] must be finite and nonzero, mean[c] finite.
+ */
+typedef struct {
+    uint32_t flags;
+    float mean[3];
+    float std[3];
+} kr_post_t;
+
+/*
+ * Bilinear resize (Sec. III "oversizing, downsizing").
+ * src: u8, HWC, C = 1 or 3. dst: same batch as src; its height and width are
+ * the output size (Sec. II-B: the caller pre-allocates the output and its size
+ * defines the operation). dst channels = src channels, or 1 with KR_GRAY
+ * (src C = 3). dst dtype KR_U8 (HWC) or KR_F32 (HWC or CHW).
+ * Returns KR_OK once the work is enqueued on `stream`.
+ */
+kr_status kr_resize_bilinear(const kr_image_t *src, const kr_image_t *dst,
+                             const kr_post_t *post, kr_stream_t stream);
+
+/*
+ * Affine warp with a 2x3 inverse map (Sec. II-A "geometric transforms";
+ * Sec. III "horizontal flip" is the map [-1 0 W; 0 1 0]).
+ * M: HOST pointer to batch x 6 floats, row-major [m00 m01 m02 m10 m11 m12]
+ * per image, mapping destination pixel centres to source pixel centres. The
+ * floats are copied before the call returns. Non-finite entries give
+ * KR_ERR_INVALID_ARG. Zero border, tap by tap. dst as for resize.
+ */
+kr_status kr_warp_affine(const kr_image_t *src, const kr_image_t *dst, const float *M,
+                         const kr_post_t *post, kr_stream_t stream);
+
+/*
+ * RGB -> gray (Sec. III "RGB to grayscale"; Sec. IV-B gray_from_rgb takes an
+ * Image<u8,3> and a pre-allocated Image<u8,1> of the same size).
+ * src: u8 HWC C = 3. dst: u8 HWC C = 1, same height, width and batch.
+ */
+kr_status kr_rgb_to_gray(const kr_image_t *src, const kr_image_t *dst, kr_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
+/* Ragged batch: many independent operations in one persistent launch.      */
+/* ------------------------------------------------------------------------ */
+
+typedef enum { KR_OP_RESIZE = 0, KR_OP_WARP = 1, KR_OP_GRAY = 2 } kr_op;
+
+/*
+ * One item of a ragged batch. src and dst follow the rules of the matching
+ * single-image call, with batch == 1. M is used by KR_OP_WARP only; post by
+ * KR_OP_RESIZE and KR_OP_WARP.
+ */
+typedef struct {
+    int32_t op;
+    kr_image_t src;
+    kr_image_t dst;
+    float M[6];
+    kr_post_t post;
+} kr_work_t;
+
+/*
+ * Launch options. tile_config: -1 = the autotuned choice for this batch's
+ * shape class (the first submit of a class tunes it, see kr_autotune_batch),
+ * or an index < kr_tile_config_count(). ctas_per_sm: 0 = the occupancy limit.
+ * use_graph: nonzero = replay the launch from a CUDA graph captured once per
+ * (stream, workspace, configuration).
+ */
+typedef struct {
+    int32_t tile_config;
+    int32_t ctas_per_sm;
+    int32_t use_graph;
+} kr_batch_opts_t;
+
+/* Device workspace bytes that kr_batch_submit needs for up to max_items items. */
+size_t kr_batch_workspace_size(int32_t max_items);
+
+/*
+ * Run n work items in one persistent launch (no counterpart in the paper:
+ * this is the batching form of the operators above).
+ * items: HOST array of n items; it is copied before the call returns.
+ * workspace: caller-owned DEVICE buffer of ws_bytes >= kr_batch_workspace_size(n);
+ * it holds the device work list and must not be used by another submit that
+ * may run concurrently. opts: NULL = defaults (autotuned tile, no graph).
+ * Each item's result equals the matching single-image call's bit for bit.
+ */
+kr_status kr_batch_submit(const kr_work_t *items, int32_t n, void *workspace,
+                          size_t ws_bytes, const kr_batch_opts_t *opts, kr_stream_t stream);
+
+/* Number of tile configurations the batch launch can use, and their shapes. */
+int32_t kr_tile_config_count(void);
+kr_status kr_tile_config_shape(int32_t index, int32_t *tile_w, int32_t *tile_h);
+
+/*
+ * Time every tile configuration x CTA count on these items (the outputs are
+ * written several times) and remember the fastest for this batch's shape
+ * class. Synchronises `stream`. best_config / best_ctas_per_sm may be NULL.
+ */
+kr_status kr_autotune_batch(const kr_work_t *items, int32_t n, void *workspace,
+                            size_t ws_bytes, kr_stream_t stream,
+                            int32_t *best_config, int32_t *best_ctas_per_sm);
+
+/* Save / load the autotune cache as a small JSON text file. */
+kr_status kr_autotune_save(const char *path);
+kr_status kr_autotune_load(const char *path);
+
+/* ------------------------------------------------------------------------ */
+/* Misc.                                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Static text for a status code. */
+const char *kr_status_string(kr_status status);
+
+/* Text of the last KR_ERR_CUDA in this thread ("" if none). */
+const char *kr_last_error(void);
+
+/* Release graphs, pinned staging and caches the library holds. Idempotent. */
+void kr_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KR_H */

@@ -1,0 +1,222 @@
+// extern "C" entry points of the single-image operators: argument validation
+// (everything is checked on the host before anything is enqueued), mapping of
+// the public descriptors to the internal launch descriptors, status text.
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "kr_device.cuh"
+#include "kr_internal.h"
+
+namespace kr {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string &what, cudaError_t e)
+{
+    g_last_error = what + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+}
+
+// Largest accepted image side.
+constexpr int kMaxSide = 65535;
+
+static int esize_of(int dtype) { return dtype == KR_F32 ? 4 : 1; }
+
+// Bytes from `data` to one past the last byte of one image.
+static int64_t image_extent(const kr_image_t &im)
+{
+    const int es = esize_of(im.dtype);
+    if (im.layout == KR_CHW)
+        return (int64_t)(im.channels - 1) * im.plane_stride + (int64_t)(im.height - 1) * im.pitch +
+               (int64_t)im.width * es;
+    return (int64_t)(im.height - 1) * im.pitch + (int64_t)im.width * im.channels * es;
+}
+
+// [lo, hi) of all bytes an image (batch) may touch.
+static void image_range(const kr_image_t &im, uintptr_t &lo, uintptr_t &hi)
+{
+    lo = (uintptr_t)im.data;
+    hi = lo + (uintptr_t)image_extent(im) + (uintptr_t)(im.batch - 1) * (uintptr_t)im.batch_stride;
+}
+
+// Structural checks shared by sources and destinations.
+static kr_status check_image(const kr_image_t *im, bool is_dst)
+{
+    if (!im || !im->data) return KR_ERR_INVALID_ARG;
+    if (im->height < 1 || im->width < 1 || im->height > kMaxSide || im->width > kMaxSide)
+        return KR_ERR_INVALID_ARG;
+    if (im->channels != 1 && im->channels != 3) return KR_ERR_INVALID_ARG;
+    if (im->dtype != KR_U8 && im->dtype != KR_F32) return KR_ERR_INVALID_ARG;
+    if (im->layout != KR_HWC && im->layout != KR_CHW) return KR_ERR_INVALID_ARG;
+    if (im->batch < 1) return KR_ERR_INVALID_ARG;
+    const int es = esize_of(im->dtype);
+    if (im->dtype == KR_F32) {
+        if (((uintptr_t)im->data | (uintptr_t)im->pitch) & 3) return KR_ERR_INVALID_ARG;
+        if (im->layout == KR_CHW && (im->plane_stride & 3)) return KR_ERR_INVALID_ARG;
+        if (im->batch > 1 && (im->batch_stride & 3)) return KR_ERR_INVALID_ARG;
+    }
+    if (im->layout == KR_CHW) {
+        if (im->dtype != KR_F32 || !is_dst) return KR_ERR_UNSUPPORTED;
+        if (im->pitch < (int64_t)im->width * 4) return KR_ERR_INVALID_ARG;
+        if (im->channels > 1 && im->plane_stride < (int64_t)(im->height - 1) * im->pitch + im->width * 4)
+            return KR_ERR_INVALID_ARG;
+    } else {
+        if (im->pitch < (int64_t)im->width * im->channels * es) return KR_ERR_INVALID_ARG;
+    }
+    if (im->batch > 1) {
+        if (im->batch_stride < 0) return KR_ERR_INVALID_ARG;
+        // destinations may not overlap between images; sources may (e.g. stride 0)
+        if (is_dst && im->batch_stride < image_extent(*im)) return KR_ERR_INVALID_ARG;
+    }
+    return KR_OK;
+}
+
+static kr_status check_alias(const kr_image_t &a, const kr_image_t &b)
+{
+    uintptr_t alo, ahi, blo, bhi;
+    image_range(a, alo, ahi);
+    image_range(b, blo, bhi);
+    return (alo < bhi && blo < ahi) ? KR_ERR_ALIAS : KR_OK;
+}
+
+// Validate the common part of resize/warp and fill the internal descriptor.
+kr_status build_resample(int op, const kr_image_t *src, const kr_image_t *dst, const kr_post_t *post,
+                         OpDesc &d)
+{
+    kr_status st;
+    if ((st = check_image(src, false)) != KR_OK) return st;
+    if ((st = check_image(dst, true)) != KR_OK) return st;
+    if (src->dtype != KR_U8) return KR_ERR_UNSUPPORTED;
+    if (src->batch != dst->batch) return KR_ERR_INVALID_ARG;
+    const uint32_t flags = post ? post->flags : 0u;
+    if (flags & ~(KR_GRAY | KR_NORMALIZE)) return KR_ERR_INVALID_ARG;
+    const bool gray = flags & KR_GRAY, norm = flags & KR_NORMALIZE;
+    if (gray) {
+        if (src->channels != 3 || dst->channels != 1) return KR_ERR_INVALID_ARG;
+    } else if (dst->channels != src->channels) {
+        return KR_ERR_INVALID_ARG;
+    }
+    if (norm && dst->dtype != KR_F32) return KR_ERR_INVALID_ARG;
+    if (dst->dtype == KR_U8 && dst->layout != KR_HWC) return KR_ERR_INVALID_ARG;
+    if ((st = check_alias(*src, *dst)) != KR_OK) return st;
+
+    std::memset(&d, 0, sizeof(d));
+    d.op = op;
+    d.cin = src->channels;
+    d.outk = dst->dtype == KR_U8 ? (gray ? OUT_U8_GRAY : OUT_U8) : (gray ? OUT_F32_GRAY : OUT_F32);
+    d.src = (const uint8_t *)src->data;
+    d.spitch = src->pitch;
+    d.sbatch = src->batch > 1 ? src->batch_stride : 0;
+    d.H = src->height;
+    d.W = src->width;
+    d.dst = (uint8_t *)dst->data;
+    d.dpitch = dst->pitch;
+    d.dplane = dst->layout == KR_CHW ? dst->plane_stride : 0;
+    d.dbatch = dst->batch > 1 ? dst->batch_stride : 0;
+    d.h = dst->height;
+    d.w = dst->width;
+    d.chw = dst->layout == KR_CHW && dst->channels == 3;
+    d.batch = src->batch;
+    for (int c = 0; c < 3; ++c) {
+        double mean = 0.0, stdv = 1.0;
+        if (norm) {
+            mean = post->mean[c];
+            stdv = post->std[c];
+            if (!std::isfinite(mean) || !std::isfinite(stdv) || stdv == 0.0) return KR_ERR_INVALID_ARG;
+        }
+        d.scale[c] = (float)(1.0 / (255.0 * stdv));
+        d.bias[c] = (float)(-mean / stdv);
+    }
+    return KR_OK;
+}
+
+kr_status build_gray(const kr_image_t *src, const kr_image_t *dst, GrayDesc &d)
+{
+    kr_status st;
+    if ((st = check_image(src, false)) != KR_OK) return st;
+    if ((st = check_image(dst, true)) != KR_OK) return st;
+    if (src->dtype != KR_U8 || dst->dtype != KR_U8 || dst->layout != KR_HWC) return KR_ERR_UNSUPPORTED;
+    if (src->channels != 3 || dst->channels != 1) return KR_ERR_INVALID_ARG;
+    if (src->height != dst->height || src->width != dst->width || src->batch != dst->batch)
+        return KR_ERR_INVALID_ARG;
+    if ((st = check_alias(*src, *dst)) != KR_OK) return st;
+    d.src = (const uint8_t *)src->data;
+    d.spitch = src->pitch;
+    d.sbatch = src->batch > 1 ? src->batch_stride : 0;
+    d.dst = (uint8_t *)dst->data;
+    d.dpitch = dst->pitch;
+    d.dbatch = dst->batch > 1 ? dst->batch_stride : 0;
+    d.H = src->height;
+    d.W = src->width;
+    d.batch = src->batch;
+    return KR_OK;
+}
+
+}  // namespace kr
+
+using namespace kr;
+
+extern "C" {
+
+kr_status kr_resize_bilinear(const kr_image_t *src, const kr_image_t *dst, const kr_post_t *post,
+                             kr_stream_t stream)
+{
+    OpDesc d;
+    kr_status st = build_resample(OP_RESIZE, src, dst, post, d);
+    if (st != KR_OK) return st;
+    cudaError_t e = launch_resample(d, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_last_error("kr_resize_bilinear", e);
+        return KR_ERR_CUDA;
+    }
+    return KR_OK;
+}
+
+kr_status kr_warp_affine(const kr_image_t *src, const kr_image_t *dst, const float *M,
+                         const kr_post_t *post, kr_stream_t stream)
+{
+    if (!M) return KR_ERR_INVALID_ARG;
+    OpDesc d;
+    kr_status st = build_resample(OP_WARP, src, dst, post, d);
+    if (st != KR_OK) return st;
+    for (int64_t i = 0; i < (int64_t)d.batch * 6; ++i)
+        if (!std::isfinite(M[i])) return KR_ERR_INVALID_ARG;
+    d.M = M;
+    cudaError_t e = launch_resample(d, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_last_error("kr_warp_affine", e);
+        return KR_ERR_CUDA;
+    }
+    return KR_OK;
+}
+
+kr_status kr_rgb_to_gray(const kr_image_t *src, const kr_image_t *dst, kr_stream_t stream)
+{
+    GrayDesc d;
+    kr_status st = build_gray(src, dst, d);
+    if (st != KR_OK) return st;
+    cudaError_t e = launch_gray(d, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_last_error("kr_rgb_to_gray", e);
+        return KR_ERR_CUDA;
+    }
+    return KR_OK;
+}
+
+const char *kr_status_string(kr_status s)
+{
+    switch (s) {
+    case KR_OK: return "ok";
+    case KR_ERR_INVALID_ARG: return "invalid argument";
+    case KR_ERR_UNSUPPORTED: return "unsupported combination";
+    case KR_ERR_ALIAS: return "source and destination overlap";
+    case KR_ERR_CUDA: return "CUDA error";
+    case KR_ERR_NO_SPACE: return "workspace or memory budget too small";
+    case KR_ERR_TIMEOUT: return "bounded wait timed out";
+    }
+    return "unknown status";
+}
+
+const char *kr_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

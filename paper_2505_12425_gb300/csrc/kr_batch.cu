@@ -1,0 +1,567 @@
+// Ragged batches: many independent resize / warp / gray items of different
+// sizes, matrices and output sizes in ONE persistent launch.
+//
+//   host:   validate every item -> pack a work list {header, items, tile prefix}
+//           into a pinned staging slot -> one async H2D copy into the caller's
+//           workspace -> one persistent kernel (optionally both replayed from a
+//           CUDA graph);
+//   device: #SM x k CTAs pull tile indices from an atomic counter in the
+//           workspace header, find the owning item by binary search over the
+//           tile prefix, and run the same tile engine as the single-image
+//           kernels for that item's (op, channels, output kind).
+//
+// The tile shape (and CTAs per SM) comes from a small autotuner that times
+// every configuration on the batch and caches the winner per batch class.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kr_device.cuh"
+#include "kr_internal.h"
+
+namespace kr {
+
+// ---------------------------------------------------------------------------
+// Device work list
+// ---------------------------------------------------------------------------
+struct alignas(16) WorkItem {
+    const uint8_t *src;
+    uint8_t *dst;
+    int64_t spitch, dpitch, dplane;
+    int32_t H, W, h, w;
+    int32_t kind;          // KIND_* below
+    int32_t tiles_x;
+    int32_t foot_budget;
+    int32_t chw;
+    float M[6];
+    float scale[3], bias[3];
+    int32_t pad[2];
+};
+static_assert(sizeof(WorkItem) == 128, "work item is 128 bytes");
+
+struct alignas(16) WsHeader {
+    unsigned next;         // tile counter (0 in every freshly copied header)
+    int n;                 // items
+    int total_tiles;
+    int pad[61];
+};
+static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
+
+constexpr int kind_of(int op, int cin, int outk) { return op | (cin << 4) | (outk << 8); }
+constexpr int KIND_GRAY = 0x1000;
+
+static size_t prefix_bytes(int n) { return ((size_t)(n + 1) * 4 + 15) & ~(size_t)15; }
+static size_t worklist_bytes(int n) { return sizeof(WsHeader) + (size_t)n * sizeof(WorkItem) + prefix_bytes(n); }
+
+// Gray tile: TW x TH pixels, no staging (3 bytes in, 1 byte out per pixel).
+template <int TW, int TH>
+__device__ __forceinline__ void gray_tile(const WorkItem &it, int tx, int ty)
+{
+    const int x0 = tx * TW, y0 = ty * TH;
+    const int nx = min(TW, it.w - x0), ny = min(TH, it.h - y0);
+    for (int i = threadIdx.x; i < nx * ny; i += kThreads) {
+        const int r = i / nx, c = i - r * nx;
+        const uint8_t *s = it.src + (int64_t)(y0 + r) * it.spitch + (int64_t)(x0 + c) * 3;
+        it.dst[(int64_t)(y0 + r) * it.dpitch + x0 + c] = (uint8_t)gray_u8(__ldg(s), __ldg(s + 1), __ldg(s + 2));
+    }
+}
+
+__device__ __forceinline__ Job job_of(const WorkItem &it)
+{
+    Job J;
+    J.src = it.src;
+    J.spitch = it.spitch;
+    J.H = it.H;
+    J.W = it.W;
+    J.dst = it.dst;
+    J.dpitch = it.dpitch;
+    J.dplane = it.dplane;
+    J.h = it.h;
+    J.w = it.w;
+    J.chw = it.chw;
+    J.foot_budget = it.foot_budget;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) J.M[k] = it.M[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        J.scale[k] = it.scale[k];
+        J.bias[k] = it.bias[k];
+    }
+    return J;
+}
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(kThreads) ragged_kernel(uint8_t *ws)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ TileShared<TW, TH> ts;
+    __shared__ int s_tile;
+    WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
+    const WorkItem *items = reinterpret_cast<const WorkItem *>(ws + sizeof(WsHeader));
+    const int n = hdr->n, total = hdr->total_tiles;
+    const int *prefix = reinterpret_cast<const int *>(items + n);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&hdr->next, 1u);
+        __syncthreads();
+        const int t = s_tile;
+        if (t >= total) break;
+        int lo = 0, hi = n - 1;   // last item whose first tile is <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(prefix + mid) <= t) lo = mid; else hi = mid - 1;
+        }
+        const WorkItem &it = items[lo];
+        const int local = t - __ldg(prefix + lo);
+        const int ty = local / it.tiles_x, tx = local - ty * it.tiles_x;
+        if (it.kind == KIND_GRAY) {
+            gray_tile<TW, TH>(it, tx, ty);
+        } else {
+            const Job J = job_of(it);
+            switch (it.kind) {
+#define KR_CASE(OP, CIN, OUTK) \
+    case kind_of(OP, CIN, OUTK): process_tile<OP, CIN, OUTK, TW, TH>(J, tx, ty, smem, ts); break;
+            KR_CASE(OP_RESIZE, 3, OUT_U8)
+            KR_CASE(OP_RESIZE, 3, OUT_U8_GRAY)
+            KR_CASE(OP_RESIZE, 3, OUT_F32)
+            KR_CASE(OP_RESIZE, 3, OUT_F32_GRAY)
+            KR_CASE(OP_RESIZE, 1, OUT_U8)
+            KR_CASE(OP_RESIZE, 1, OUT_F32)
+            KR_CASE(OP_WARP, 3, OUT_U8)
+            KR_CASE(OP_WARP, 3, OUT_U8_GRAY)
+            KR_CASE(OP_WARP, 3, OUT_F32)
+            KR_CASE(OP_WARP, 3, OUT_F32_GRAY)
+            KR_CASE(OP_WARP, 1, OUT_U8)
+            KR_CASE(OP_WARP, 1, OUT_F32)
+#undef KR_CASE
+            default: break;
+            }
+        }
+        __syncthreads();   // everyone has read s_tile before thread 0 rewrites it
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tile configurations
+// ---------------------------------------------------------------------------
+struct TileCfg {
+    int tw, th;
+    const void *kernel;
+    int max_smem;
+};
+
+template <int TW, int TH> static constexpr int max_out_stage() { return 3 * TH * round16(TW * 4 + 15); }
+
+static TileCfg g_cfgs[] = {
+    {64, 32, (const void *)ragged_kernel<64, 32>, kFootCap + max_out_stage<64, 32>()},
+    {32, 32, (const void *)ragged_kernel<32, 32>, kFootCap + max_out_stage<32, 32>()},
+    {128, 16, (const void *)ragged_kernel<128, 16>, kFootCap + max_out_stage<128, 16>()},
+    {64, 16, (const void *)ragged_kernel<64, 16>, kFootCap + max_out_stage<64, 16>()},
+};
+constexpr int kNumCfgs = sizeof(g_cfgs) / sizeof(g_cfgs[0]);
+
+static int out_stage_of(int outk, int cin, int tw, int th)
+{
+    const bool f32 = outk == OUT_F32 || outk == OUT_F32_GRAY;
+    const int dC = (outk == OUT_U8_GRAY || outk == OUT_F32_GRAY) ? 1 : cin;
+    return f32 ? dC * th * round16(tw * 4 + 15) : th * round16(tw * dC + 15);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side packing
+// ---------------------------------------------------------------------------
+struct Packed {
+    std::vector<WorkItem> items;
+    std::vector<int> prefix;
+    int total_tiles = 0;
+    size_t smem = 0;        // dynamic shared bytes the launch needs
+    int opmask = 0;
+    double out_px = 0;
+};
+
+// Validate all items and convert them into device work items for tile shape (tw, th).
+static kr_status pack_items(const kr_work_t *items, int n, int tw, int th, Packed &P)
+{
+    P.items.resize(n);
+    P.prefix.resize(n + 1);
+    P.total_tiles = 0;
+    P.smem = 0;
+    P.opmask = 0;
+    P.out_px = 0;
+    long long total = 0;
+    for (int i = 0; i < n; ++i) {
+        const kr_work_t &w = items[i];
+        if (w.src.batch != 1 || w.dst.batch != 1) return KR_ERR_INVALID_ARG;
+        WorkItem &it = P.items[i];
+        std::memset(&it, 0, sizeof(it));
+        if (w.op == KR_OP_GRAY) {
+            GrayDesc g;
+            kr_status st = build_gray(&w.src, &w.dst, g);
+            if (st != KR_OK) return st;
+            it.src = g.src; it.dst = g.dst; it.spitch = g.spitch; it.dpitch = g.dpitch;
+            it.H = it.h = g.H; it.W = it.w = g.W;
+            it.kind = KIND_GRAY;
+        } else if (w.op == KR_OP_RESIZE || w.op == KR_OP_WARP) {
+            const int op = w.op == KR_OP_RESIZE ? OP_RESIZE : OP_WARP;
+            OpDesc d;
+            kr_status st = build_resample(op, &w.src, &w.dst, &w.post, d);
+            if (st != KR_OK) return st;
+            if (op == OP_WARP)
+                for (int k = 0; k < 6; ++k)
+                    if (!std::isfinite(w.M[k])) return KR_ERR_INVALID_ARG;
+            it.src = d.src; it.dst = d.dst; it.spitch = d.spitch; it.dpitch = d.dpitch;
+            it.dplane = d.dplane; it.H = d.H; it.W = d.W; it.h = d.h; it.w = d.w; it.chw = d.chw;
+            it.kind = kind_of(op, d.cin, d.outk);
+            for (int k = 0; k < 6; ++k) it.M[k] = op == OP_WARP ? w.M[k] : 0.f;
+            for (int k = 0; k < 3; ++k) { it.scale[k] = d.scale[k]; it.bias[k] = d.bias[k]; }
+            it.foot_budget = op == OP_RESIZE ? foot_budget_resize(d.cin, d.H, d.W, d.h, d.w, tw, th)
+                                             : foot_budget_warp(d.cin, d.H, d.W, it.M, tw, th);
+            P.smem = std::max(P.smem, (size_t)it.foot_budget + out_stage_of(d.outk, d.cin, tw, th));
+        } else {
+            return KR_ERR_INVALID_ARG;
+        }
+        P.opmask |= 1 << w.op;
+        P.out_px += (double)it.h * it.w;
+        it.tiles_x = (it.w + tw - 1) / tw;
+        const long long tiles = (long long)it.tiles_x * ((it.h + th - 1) / th);
+        P.prefix[i] = (int)total;
+        total += tiles;
+        if (total > 0x7FFFFFFF) return KR_ERR_INVALID_ARG;
+    }
+    P.prefix[n] = (int)total;
+    P.total_tiles = (int)total;
+    return KR_OK;
+}
+
+static void write_worklist(const Packed &P, uint8_t *dst)
+{
+    WsHeader h;
+    std::memset(&h, 0, sizeof(h));
+    h.next = 0;
+    h.n = (int)P.items.size();
+    h.total_tiles = P.total_tiles;
+    std::memcpy(dst, &h, sizeof(h));
+    std::memcpy(dst + sizeof(h), P.items.data(), P.items.size() * sizeof(WorkItem));
+    std::memcpy(dst + sizeof(h) + P.items.size() * sizeof(WorkItem), P.prefix.data(), P.prefix.size() * 4);
+}
+
+// ---------------------------------------------------------------------------
+// Per-workspace submit contexts: pinned staging ring + graphs.
+// ---------------------------------------------------------------------------
+constexpr int kSlots = 4;
+
+struct GraphEntry {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t copy = nullptr;
+};
+
+struct Ctx {
+    size_t cap = 0;
+    uint8_t *slot[kSlots] = {};
+    cudaEvent_t done[kSlots] = {};
+    int next = 0;
+    std::map<std::string, GraphEntry> graphs;   // key: stream|cfg|ctas
+};
+
+static std::mutex g_mu;
+static std::map<void *, Ctx> g_ctx;
+static std::map<std::string, std::pair<int, int>> g_tune;   // batch class -> (cfg, ctas/SM)
+
+static void free_ctx(Ctx &c)
+{
+    for (auto &kv : c.graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        if (kv.second.graph) cudaGraphDestroy(kv.second.graph);
+    }
+    c.graphs.clear();
+    for (int i = 0; i < kSlots; ++i) {
+        if (c.done[i]) { cudaEventSynchronize(c.done[i]); cudaEventDestroy(c.done[i]); }
+        if (c.slot[i]) cudaFreeHost(c.slot[i]);
+        c.done[i] = nullptr;
+        c.slot[i] = nullptr;
+    }
+    c.cap = 0;
+}
+
+static cudaError_t ctx_for(void *ws, size_t cap, Ctx *&out)
+{
+    Ctx &c = g_ctx[ws];
+    if (c.cap < cap) {
+        free_ctx(c);
+        for (int i = 0; i < kSlots; ++i) {
+            cudaError_t e = cudaHostAlloc((void **)&c.slot[i], cap, cudaHostAllocDefault);
+            if (e != cudaSuccess) { free_ctx(c); return e; }
+            e = cudaEventCreateWithFlags(&c.done[i], cudaEventDisableTiming);
+            if (e != cudaSuccess) { free_ctx(c); return e; }
+        }
+        c.cap = cap;
+    }
+    out = &c;
+    return cudaSuccess;
+}
+
+static int sm_count()
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+static cudaError_t prepare_cfg(int cfg, size_t smem, int &occ)
+{
+    const TileCfg &c = g_cfgs[cfg];
+    cudaError_t e = cudaFuncSetAttribute(c.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c.max_smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.kernel, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    occ = std::max(occ, 1);
+    return cudaSuccess;
+}
+
+static std::string class_key(const Packed &P, int n)
+{
+    char b[160];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, dev);
+    const int nb = (int)std::floor(std::log2((double)std::max(n, 1)));
+    const int pb = (int)std::floor(std::log2(std::max(P.out_px, 1.0)));
+    std::snprintf(b, sizeof(b), "%s|n2^%d|px2^%d|ops%d", prop.name, nb, pb, P.opmask);
+    return b;
+}
+
+// Enqueue one packed batch: copy the work list, launch the persistent kernel.
+static kr_status enqueue(const Packed &P, void *ws, int cfg, int ctas_per_sm, bool use_graph,
+                         cudaStream_t stream, const char *where)
+{
+    const size_t bytes = worklist_bytes((int)P.items.size());
+    int occ = 1;
+    cudaError_t e = prepare_cfg(cfg, P.smem, occ);
+    if (e != cudaSuccess) { set_last_error(where, e); return KR_ERR_CUDA; }
+    const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+    const int grid = std::max(1, std::min(sm_count() * per_sm, P.total_tiles));
+
+    std::lock_guard<std::mutex> lk(g_mu);
+    Ctx *c = nullptr;
+    e = ctx_for(ws, bytes, c);
+    if (e != cudaSuccess) { set_last_error(where, e); return KR_ERR_CUDA; }
+    const int s = c->next;
+    c->next = (c->next + 1) % kSlots;
+    e = cudaEventSynchronize(c->done[s]);   // the slot's previous copy has finished
+    if (e != cudaSuccess) { set_last_error(where, e); return KR_ERR_CUDA; }
+    write_worklist(P, c->slot[s]);
+
+    if (!use_graph) {
+        e = cudaMemcpyAsync(ws, c->slot[s], bytes, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) {
+            void *args[] = {&ws};
+            e = cudaLaunchKernel(g_cfgs[cfg].kernel, dim3(grid), dim3(kThreads), args, P.smem, stream);
+        }
+    } else {
+        char key[96];
+        std::snprintf(key, sizeof(key), "%p|%d|%d|%zu", (void *)stream, cfg, grid, P.smem);
+        GraphEntry &g = c->graphs[key];
+        if (!g.exec) {
+            e = cudaGraphCreate(&g.graph, 0);
+            cudaGraphNode_t kn = nullptr;
+            if (e == cudaSuccess)
+                e = cudaGraphAddMemcpyNode1D(&g.copy, g.graph, nullptr, 0, ws, c->slot[s], bytes,
+                                             cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) {
+                cudaKernelNodeParams kp;
+                std::memset(&kp, 0, sizeof(kp));
+                void *args[] = {&ws};
+                kp.func = (void *)g_cfgs[cfg].kernel;
+                kp.gridDim = dim3(grid);
+                kp.blockDim = dim3(kThreads);
+                kp.sharedMemBytes = (unsigned)P.smem;
+                kp.kernelParams = args;
+                e = cudaGraphAddKernelNode(&kn, g.graph, &g.copy, 1, &kp);
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+            if (e != cudaSuccess) {
+                if (g.graph) cudaGraphDestroy(g.graph);
+                c->graphs.erase(key);
+                set_last_error(where, e);
+                return KR_ERR_CUDA;
+            }
+        } else {
+            e = cudaGraphExecMemcpyNodeSetParams1D(g.exec, g.copy, ws, c->slot[s], bytes,
+                                                   cudaMemcpyHostToDevice);
+        }
+        if (e == cudaSuccess) e = cudaGraphLaunch(g.exec, stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(c->done[s], stream);
+    if (e != cudaSuccess) { set_last_error(where, e); return KR_ERR_CUDA; }
+    return KR_OK;
+}
+
+}  // namespace kr
+
+using namespace kr;
+
+extern "C" {
+
+size_t kr_batch_workspace_size(int32_t max_items)
+{
+    return worklist_bytes(std::max(max_items, 1));
+}
+
+int32_t kr_tile_config_count(void) { return kNumCfgs; }
+
+kr_status kr_tile_config_shape(int32_t index, int32_t *tile_w, int32_t *tile_h)
+{
+    if (index < 0 || index >= kNumCfgs || !tile_w || !tile_h) return KR_ERR_INVALID_ARG;
+    *tile_w = g_cfgs[index].tw;
+    *tile_h = g_cfgs[index].th;
+    return KR_OK;
+}
+
+kr_status kr_batch_submit(const kr_work_t *items, int32_t n, void *workspace, size_t ws_bytes,
+                          const kr_batch_opts_t *opts, kr_stream_t stream)
+{
+    if (n < 0 || (n > 0 && (!items || !workspace))) return KR_ERR_INVALID_ARG;
+    if (n == 0) return KR_OK;
+    if (ws_bytes < worklist_bytes(n)) return KR_ERR_NO_SPACE;
+    if ((uintptr_t)workspace & 15) return KR_ERR_INVALID_ARG;
+    int cfg = opts ? opts->tile_config : -1;
+    int ctas = opts ? opts->ctas_per_sm : 0;
+    if (cfg >= kNumCfgs || ctas < 0) return KR_ERR_INVALID_ARG;
+    Packed P;
+    kr_status st;
+    if (cfg < 0) {
+        // the cached choice for this batch class, else configuration 0
+        if ((st = pack_items(items, n, g_cfgs[0].tw, g_cfgs[0].th, P)) != KR_OK) return st;
+        const std::string key = class_key(P, n);
+        int c = 0, k = ctas;
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) { c = it->second.first; if (!ctas) k = it->second.second; }
+        }
+        cfg = c;
+        ctas = k;
+        if (cfg != 0 && (st = pack_items(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th, P)) != KR_OK) return st;
+    } else if ((st = pack_items(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th, P)) != KR_OK) {
+        return st;
+    }
+    // every item must fit in shared memory at this tile shape
+    if (P.smem > (size_t)g_cfgs[cfg].max_smem) return KR_ERR_UNSUPPORTED;
+    return enqueue(P, workspace, cfg, ctas, opts && opts->use_graph, (cudaStream_t)stream,
+                   "kr_batch_submit");
+}
+
+kr_status kr_autotune_batch(const kr_work_t *items, int32_t n, void *workspace, size_t ws_bytes,
+                            kr_stream_t stream, int32_t *best_config, int32_t *best_ctas_per_sm)
+{
+    if (n < 1 || !items || !workspace) return KR_ERR_INVALID_ARG;
+    if (ws_bytes < worklist_bytes(n)) return KR_ERR_NO_SPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return KR_ERR_CUDA;
+    float best = 1e30f;
+    int bc = 0, bk = 0;
+    std::string key;
+    kr_status result = KR_OK;
+    for (int cfg = 0; cfg < kNumCfgs && result == KR_OK; ++cfg) {
+        Packed P;
+        kr_status st = pack_items(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th, P);
+        if (st != KR_OK) { result = st; break; }
+        if (cfg == 0) key = class_key(P, n);
+        if (P.smem > (size_t)g_cfgs[cfg].max_smem) continue;
+        int occ = 1;
+        if (prepare_cfg(cfg, P.smem, occ) != cudaSuccess) { result = KR_ERR_CUDA; break; }
+        for (int k = 1; k <= occ; ++k) {
+            if (k > 2 && k < occ) continue;   // candidates: 1, 2 and the occupancy limit
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 4 && result == KR_OK; ++rep) {
+                cudaEventRecord(e0, s);
+                st = enqueue(P, workspace, cfg, k, false, s, "kr_autotune_batch");
+                cudaEventRecord(e1, s);
+                if (st != KR_OK) { result = st; break; }
+                if (cudaEventSynchronize(e1) != cudaSuccess) { result = KR_ERR_CUDA; break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ms_best = std::min(ms_best, ms);   // rep 0 warms up
+            }
+            if (ms_best < best) { best = ms_best; bc = cfg; bk = k; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result != KR_OK) return result;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_tune[key] = {bc, bk};
+    }
+    if (best_config) *best_config = bc;
+    if (best_ctas_per_sm) *best_ctas_per_sm = bk;
+    return KR_OK;
+}
+
+kr_status kr_autotune_save(const char *path)
+{
+    if (!path) return KR_ERR_INVALID_ARG;
+    FILE *f = std::fopen(path, "w");
+    if (!f) return KR_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    std::fprintf(f, "{\"entries\": [\n");
+    size_t i = 0;
+    for (auto &kv : g_tune) {
+        std::fprintf(f, "  {\"key\": \"%s\", \"tile_config\": %d, \"ctas_per_sm\": %d}%s\n", kv.first.c_str(),
+                     kv.second.first, kv.second.second, ++i < g_tune.size() ? "," : "");
+    }
+    std::fprintf(f, "]}\n");
+    std::fclose(f);
+    return KR_OK;
+}
+
+kr_status kr_autotune_load(const char *path)
+{
+    if (!path) return KR_ERR_INVALID_ARG;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return KR_ERR_INVALID_ARG;
+    std::string text;
+    char buf[4096];
+    size_t r;
+    while ((r = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, r);
+    std::fclose(f);
+    std::map<std::string, std::pair<int, int>> got;
+    size_t pos = 0;
+    while ((pos = text.find("\"key\": \"", pos)) != std::string::npos) {
+        pos += 8;
+        const size_t end = text.find('"', pos);
+        if (end == std::string::npos) return KR_ERR_INVALID_ARG;
+        const std::string key = text.substr(pos, end - pos);
+        int cfg = -1, ctas = -1;
+        const size_t pc = text.find("\"tile_config\":", end), pk = text.find("\"ctas_per_sm\":", end);
+        if (pc == std::string::npos || pk == std::string::npos) return KR_ERR_INVALID_ARG;
+        if (std::sscanf(text.c_str() + pc + 14, "%d", &cfg) != 1 ||
+            std::sscanf(text.c_str() + pk + 14, "%d", &ctas) != 1)
+            return KR_ERR_INVALID_ARG;
+        if (cfg < 0 || cfg >= kNumCfgs || ctas < 1) return KR_ERR_INVALID_ARG;
+        got[key] = {cfg, ctas};
+        pos = end;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto &kv : got) g_tune[kv.first] = kv.second;
+    return KR_OK;
+}
+
+void kr_shutdown(void)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto &kv : g_ctx) free_ctx(kv.second);
+    g_ctx.clear();
+    g_tune.clear();
+}
+
+}  // extern "C"

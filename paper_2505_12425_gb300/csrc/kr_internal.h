@@ -1,0 +1,61 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/kr.h"
+
+namespace kr {
+
+// Largest number of per-image warp matrices carried by one launch's parameters.
+constexpr int kMaxMPerLaunch = 128;
+// Shared-memory cap for one tile's source footprint.
+constexpr int kFootCap = 40 * 1024;
+
+// A validated single-image-op request, pointers as device addresses.
+struct OpDesc {
+    int op;          // OP_RESIZE / OP_WARP
+    int cin;         // source channels (1 or 3)
+    int outk;        // OUT_U8 / OUT_U8_GRAY / OUT_F32 / OUT_F32_GRAY
+    const uint8_t *src;
+    int64_t spitch, sbatch;
+    int H, W;
+    uint8_t *dst;
+    int64_t dpitch, dplane, dbatch;
+    int h, w;
+    int chw;
+    int batch;
+    float scale[3], bias[3];
+    const float *M;  // host, 6 * batch floats (warp)
+};
+
+// Per-op launch (per-image tiles, blockIdx.z = image). Returns cudaSuccess or the launch error.
+cudaError_t launch_resample(const OpDesc &d, cudaStream_t stream);
+
+// Standalone RGB -> gray.
+struct GrayDesc {
+    const uint8_t *src;
+    int64_t spitch, sbatch;
+    uint8_t *dst;
+    int64_t dpitch, dbatch;
+    int H, W, batch;
+};
+cudaError_t launch_gray(const GrayDesc &d, cudaStream_t stream);
+
+// Shared-memory footprint budget of one tile (bytes, multiple of 16; 0 = no staging).
+int foot_budget_resize(int cin, int H, int W, int h, int w, int tw, int th);
+int foot_budget_warp(int cin, int H, int W, const float *M, int tw, int th);
+
+// Validation + descriptor construction (kr_abi.cu); nothing is enqueued.
+kr_status build_resample(int op, const kr_image_t *src, const kr_image_t *dst, const kr_post_t *post,
+                         OpDesc &d);
+kr_status build_gray(const kr_image_t *src, const kr_image_t *dst, GrayDesc &d);
+
+// Thread-local last CUDA error text.
+void set_last_error(const std::string &what, cudaError_t e);
+
+}  // namespace kr

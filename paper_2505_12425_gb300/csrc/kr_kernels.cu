@@ -1,0 +1,242 @@
+// Per-operation kernels: resize / warp over a batch of equally sized images
+// (one TW x TH output tile per CTA, blockIdx.z = image) and the standalone
+// RGB -> gray streaming kernel.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "kr_device.cuh"
+#include "kr_internal.h"
+
+namespace kr {
+
+// Tile shape of the per-operation kernels.
+constexpr int kTW = 64;
+constexpr int kTH = 32;
+
+struct OpParams {
+    const uint8_t *src;
+    int64_t spitch, sbatch;
+    int32_t H, W;
+    uint8_t *dst;
+    int64_t dpitch, dplane, dbatch;
+    int32_t h, w;
+    int32_t chw;
+    int32_t foot_budget;
+    float scale[3], bias[3];
+    float M[kMaxMPerLaunch][6];
+};
+
+template <int OP, int CIN, int OUTK, int TW, int TH>
+__global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constant__ OpParams p)
+{
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ TileShared<TW, TH> ts;
+    const int z = blockIdx.z;
+    Job J;
+    J.src = p.src + (int64_t)z * p.sbatch;
+    J.spitch = p.spitch;
+    J.H = p.H;
+    J.W = p.W;
+    J.dst = p.dst + (int64_t)z * p.dbatch;
+    J.dpitch = p.dpitch;
+    J.dplane = p.dplane;
+    J.h = p.h;
+    J.w = p.w;
+    J.chw = p.chw;
+    J.foot_budget = p.foot_budget;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) J.M[k] = OP == OP_WARP ? p.M[z][k] : 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        J.scale[k] = p.scale[k];
+        J.bias[k] = p.bias[k];
+    }
+    process_tile<OP, CIN, OUTK, TW, TH>(J, blockIdx.x, blockIdx.y, smem, ts);
+}
+
+// ---------------------------------------------------------------------------
+// Footprint budgets
+// ---------------------------------------------------------------------------
+int foot_budget_resize(int cin, int H, int W, int h, int w, int tw, int th)
+{
+    // Taps of tw consecutive columns span at most (tw - 1) W / w + 2 source columns.
+    const double cols = std::ceil((tw - 1) * (double)W / w) + 3;
+    const double rows = std::ceil((th - 1) * (double)H / h) + 3;
+    const double c = std::min<double>(cols, W), r = std::min<double>(rows, H);
+    const double need = r * round16((int)c * cin + 15) + 16;
+    return need <= kFootCap ? round16((int)need) : 0;
+}
+
+int foot_budget_warp(int cin, int H, int W, const float *M, int tw, int th)
+{
+    // The staged box of a tile spans at most |m00|(tw-1) + |m01|(th-1) columns plus
+    // five (floor, the second tap, one pixel of rounding margin on each side).
+    const double cols = std::ceil(std::fabs(M[0]) * (tw - 1) + std::fabs(M[1]) * (th - 1)) + 6;
+    const double rows = std::ceil(std::fabs(M[3]) * (tw - 1) + std::fabs(M[4]) * (th - 1)) + 6;
+    if (!(cols < 1e7 && rows < 1e7)) return kFootCap;
+    const double c = std::min<double>(cols, W), r = std::min<double>(rows, H);
+    const double need = r * round16((int)c * cin + 15) + 16;
+    return round16((int)std::min<double>(need, kFootCap));
+}
+
+// ---------------------------------------------------------------------------
+// Per-operation launch
+// ---------------------------------------------------------------------------
+template <int OP, int CIN, int OUTK>
+static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
+{
+    constexpr int TW = kTW, TH = kTH;
+    auto kern = resample_kernel<OP, CIN, OUTK, TW, TH>;
+    static unsigned attr_done = 0;   // one bit per device ordinal (< 32)
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 32 || !(attr_done & (1u << dev))) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kFootCap + out_stage_bytes<OUTK, CIN, TW, TH>());
+        if (e != cudaSuccess) return e;
+        if (dev < 32) __atomic_fetch_or(&attr_done, 1u << dev, __ATOMIC_RELAXED);
+    }
+    OpParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.src = d.src;
+    p.spitch = d.spitch;
+    p.sbatch = d.sbatch;
+    p.H = d.H;
+    p.W = d.W;
+    p.dst = d.dst;
+    p.dpitch = d.dpitch;
+    p.dplane = d.dplane;
+    p.dbatch = d.dbatch;
+    p.h = d.h;
+    p.w = d.w;
+    p.chw = d.chw;
+    for (int k = 0; k < 3; ++k) {
+        p.scale[k] = d.scale[k];
+        p.bias[k] = d.bias[k];
+    }
+    const int tiles_x = (d.w + TW - 1) / TW, tiles_y = (d.h + TH - 1) / TH;
+    const int per_launch = OP == OP_WARP ? kMaxMPerLaunch : 65535;
+    for (int b0 = 0; b0 < d.batch; b0 += per_launch) {
+        const int nb = std::min(per_launch, d.batch - b0);
+        int budget = 0;
+        if (OP == OP_RESIZE) {
+            budget = foot_budget_resize(CIN, d.H, d.W, d.h, d.w, TW, TH);
+        } else {
+            for (int i = 0; i < nb; ++i) {
+                for (int k = 0; k < 6; ++k) p.M[i][k] = d.M[(size_t)(b0 + i) * 6 + k];
+                budget = std::max(budget, foot_budget_warp(CIN, d.H, d.W, p.M[i], TW, TH));
+            }
+        }
+        p.foot_budget = budget;
+        p.src = d.src + (int64_t)b0 * d.sbatch;
+        p.dst = d.dst + (int64_t)b0 * d.dbatch;
+        const size_t smem = (size_t)budget + out_stage_bytes<OUTK, CIN, TW, TH>();
+        dim3 grid(tiles_x, tiles_y, nb);
+        kern<<<grid, kThreads, smem, stream>>>(p);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <int OP>
+static cudaError_t launch_op(const OpDesc &d, cudaStream_t s)
+{
+    if (d.cin == 3) {
+        switch (d.outk) {
+        case OUT_U8: return launch_t<OP, 3, OUT_U8>(d, s);
+        case OUT_U8_GRAY: return launch_t<OP, 3, OUT_U8_GRAY>(d, s);
+        case OUT_F32: return launch_t<OP, 3, OUT_F32>(d, s);
+        case OUT_F32_GRAY: return launch_t<OP, 3, OUT_F32_GRAY>(d, s);
+        }
+    } else {
+        switch (d.outk) {
+        case OUT_U8: return launch_t<OP, 1, OUT_U8>(d, s);
+        case OUT_F32: return launch_t<OP, 1, OUT_F32>(d, s);
+        }
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_resample(const OpDesc &d, cudaStream_t stream)
+{
+    return d.op == OP_RESIZE ? launch_op<OP_RESIZE>(d, stream) : launch_op<OP_WARP>(d, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Standalone RGB -> gray: one thread per 16-pixel chunk of a row. Rows whose
+// source and destination start on 16-byte boundaries move 48 bytes in through
+// three 128-bit loads and 16 bytes out through one 128-bit store; other rows
+// and the ragged tail go pixel by pixel.
+// ---------------------------------------------------------------------------
+struct GrayParams {
+    const uint8_t *src;
+    int64_t spitch, sbatch;
+    uint8_t *dst;
+    int64_t dpitch, dbatch;
+    int32_t H, W, chunks_x;
+    int64_t total;   // batch * H * chunks_x
+};
+
+__device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[12], int b)
+{
+    return (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+}
+
+__global__ void __launch_bounds__(kThreads) gray_kernel(const __grid_constant__ GrayParams p)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.total; i += stride) {
+        const int64_t row = i / p.chunks_x;
+        const int cx = (int)(i - row * p.chunks_x);
+        const int64_t img = row / p.H;
+        const int y = (int)(row - img * p.H);
+        const uint8_t *s = p.src + img * p.sbatch + (int64_t)y * p.spitch + (int64_t)cx * 48;
+        uint8_t *d = p.dst + img * p.dbatch + (int64_t)y * p.dpitch + (int64_t)cx * 16;
+        const int n = min(16, p.W - cx * 16);
+        if (n == 16 && (((uintptr_t)s | (uintptr_t)d) & 15) == 0) {
+            uint32_t w[12];
+            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(s));
+            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(s + 16));
+            const uint4 c = __ldg(reinterpret_cast<const uint4 *>(s + 32));
+            w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+            w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+            w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
+            uint32_t o[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const uint32_t g = gray_u8(byte_of(w, 3 * k), byte_of(w, 3 * k + 1), byte_of(w, 3 * k + 2));
+                o[k >> 2] |= g << (8 * (k & 3));
+            }
+            *reinterpret_cast<uint4 *>(d) = make_uint4(o[0], o[1], o[2], o[3]);
+        } else {
+            for (int k = 0; k < n; ++k)
+                d[k] = (uint8_t)gray_u8(__ldg(s + 3 * k), __ldg(s + 3 * k + 1), __ldg(s + 3 * k + 2));
+        }
+    }
+}
+
+cudaError_t launch_gray(const GrayDesc &d, cudaStream_t stream)
+{
+    GrayParams p;
+    p.src = d.src;
+    p.spitch = d.spitch;
+    p.sbatch = d.sbatch;
+    p.dst = d.dst;
+    p.dpitch = d.dpitch;
+    p.dbatch = d.dbatch;
+    p.H = d.H;
+    p.W = d.W;
+    p.chunks_x = (d.W + 15) / 16;
+    p.total = (int64_t)d.batch * d.H * p.chunks_x;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (p.total + kThreads - 1) / kThreads;
+    const int blocks = (int)std::min<int64_t>(want, (int64_t)sms * 8);
+    gray_kernel<<<blocks, kThreads, 0, stream>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace kr

@@ -1,0 +1,313 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+u8 results are compared bit for bit; f32 results within 1e-5 absolute (the
+tolerance of the f32 path). Sizes span several tiles with ragged tails, and
+include the full-size workloads (640x480 -> 320x240; 1920x1080 resize and
+warp; 16 x 3840x2160 -> 224x224 normalised NCHW). Destinations carry guard
+bands of canary bytes that must survive every call.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2505_12425_gb300 import binding as kr
+from paper_2505_12425_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+F32_TOL = 1e-5
+CANARY_U8 = 0xA5
+CANARY_F32 = -12345.0
+MEAN, STD = inputs.IMAGENET_MEAN, inputs.IMAGENET_STD
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as ge
+    ge.build()
+    kr.load()
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+class Guarded:
+    """A destination tensor inside a canary-filled buffer (guard bands before and after)."""
+
+    def __init__(self, shape, dtype, guard=256):
+        n = int(np.prod(shape))
+        fill = CANARY_U8 if dtype == torch.uint8 else CANARY_F32
+        self.buf = torch.full((guard + n + guard,), fill, dtype=dtype, device=dev())
+        self.t = self.buf[guard:guard + n].view(*shape)
+        self.guard, self.n, self.fill = guard, n, fill
+
+    def check(self):
+        b = self.buf.cpu().numpy()
+        assert np.all(b[:self.guard] == self.fill), "write before the destination"
+        assert np.all(b[self.guard + self.n:] == self.fill), "write after the destination"
+
+    def np(self):
+        return self.t.cpu().numpy()
+
+
+def to_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev())
+
+
+# ---------------------------------------------------------------------------
+# Resize
+# ---------------------------------------------------------------------------
+RESIZE_CASES = [
+    (480, 640, 240, 320, 3),      # 640x480 -> 320x240 (full size)
+    (1080, 1920, 720, 1280, 3),   # 1920x1080 -> 1280x720 (full size)
+    (37, 53, 91, 17, 3), (100, 100, 33, 47, 1), (1, 1, 5, 7, 3), (1, 200, 1, 64, 3),
+    (200, 1, 64, 1, 1), (64, 64, 64, 64, 3), (33, 65, 130, 258, 3), (500, 700, 50, 70, 3),
+    (70, 90, 140, 181, 1), (257, 129, 65, 97, 3),
+]
+
+
+@pytest.mark.parametrize("H,W,h,w,C", RESIZE_CASES)
+def test_resize_u8(H, W, h, w, C):
+    img = inputs.uniform_image(H * 7 + W, H, W, C)
+    out = Guarded((h, w, C), torch.uint8)
+    kr.kr_resize_bilinear(to_dev(img), out.t)
+    torch.cuda.synchronize()
+    out.check()
+    np.testing.assert_array_equal(out.np(), oracle.resize_u8(img, h, w))
+
+
+@pytest.mark.parametrize("H,W,h,w", [(1080, 1920, 720, 1280), (45, 77, 100, 31), (300, 200, 37, 301)])
+def test_resize_u8_gray(H, W, h, w):
+    img = inputs.noise_gradient_image(3, H, W)
+    out = Guarded((h, w, 1), torch.uint8)
+    kr.kr_resize_bilinear(to_dev(img), out.t, gray=True)
+    torch.cuda.synchronize()
+    out.check()
+    np.testing.assert_array_equal(out.np(), oracle.resize_u8(img, h, w, gray=True))
+
+
+@pytest.mark.parametrize("layout", ["hwc", "chw"])
+@pytest.mark.parametrize("H,W,h,w,C", [(1080, 1920, 720, 1280, 3), (50, 61, 129, 33, 3), (90, 70, 45, 140, 1)])
+def test_resize_f32(H, W, h, w, C, layout):
+    img = inputs.noise_gradient_image(5, H, W, C)
+    shape = (h, w, C) if layout == "hwc" else (C, h, w)
+    out = Guarded(shape, torch.float32)
+    kr.kr_resize_bilinear(to_dev(img), out.t, mean=MEAN[:C], std=STD[:C], dst_layout=layout)
+    torch.cuda.synchronize()
+    out.check()
+    got = out.np() if layout == "hwc" else out.np().transpose(1, 2, 0)
+    ref = oracle.resize_f64(img, h, w, mean=MEAN[:C], std=STD[:C])
+    assert np.abs(got - ref).max() <= F32_TOL
+
+
+def test_resize_f32_plain_and_gray():
+    img = inputs.uniform_image(8, 123, 211, 3)
+    out = Guarded((77, 300, 3), torch.float32)
+    kr.kr_resize_bilinear(to_dev(img), out.t)      # no normalisation: p / 255
+    g = Guarded((77, 300, 1), torch.float32)
+    kr.kr_resize_bilinear(to_dev(img), g.t, gray=True, mean=MEAN, std=STD)
+    torch.cuda.synchronize()
+    out.check()
+    g.check()
+    assert np.abs(out.np() - oracle.resize_f64(img, 77, 300)).max() <= F32_TOL
+    assert np.abs(g.np() - oracle.resize_f64(img, 77, 300, gray=True, mean=MEAN, std=STD)).max() <= F32_TOL
+
+
+def test_resize_16x4k_to_224_normalised_nchw():
+    """16 uniform 3840x2160 images -> 224x224 f32 NCHW with per-channel mean/std, one launch."""
+    n, H, W = 16, 2160, 3840
+    imgs = inputs.uniform_batch(1002, n, H, W, 3)
+    src = to_dev(imgs)
+    out = Guarded((n, 3, 224, 224), torch.float32)
+    kr.kr_resize_bilinear(src, out.t, mean=MEAN, std=STD, dst_layout="chw")
+    torch.cuda.synchronize()
+    out.check()
+    got = out.np()
+    for i in range(n):
+        ref = oracle.resize_f64(imgs[i], 224, 224, mean=MEAN, std=STD)
+        assert np.abs(got[i].transpose(1, 2, 0) - ref).max() <= F32_TOL, i
+
+
+# ---------------------------------------------------------------------------
+# Warp
+# ---------------------------------------------------------------------------
+WARP_CASES = [(1080, 1920, 3, 11), (77, 131, 3, 1), (64, 64, 1, 2), (300, 41, 3, 3), (5, 9, 3, 4), (129, 257, 1, 5)]
+
+
+@pytest.mark.parametrize("H,W,C,seed", WARP_CASES)
+def test_warp_u8(H, W, C, seed):
+    img = inputs.noise_gradient_image(seed, H, W, C)
+    M = inputs.warp_matrix(seed, H, W)
+    out = Guarded((H, W, C), torch.uint8)
+    kr.kr_warp_affine(to_dev(img), out.t, M)
+    torch.cuda.synchronize()
+    out.check()
+    np.testing.assert_array_equal(out.np(), oracle.warp_u8(img, M, H, W))
+
+
+@pytest.mark.parametrize("H,W,seed", [(1080, 1920, 12), (99, 160, 3)])
+def test_warp_u8_gray(H, W, seed):
+    img = inputs.noise_gradient_image(seed, H, W)
+    M = inputs.warp_matrix(seed, H, W)
+    out = Guarded((H, W, 1), torch.uint8)
+    kr.kr_warp_affine(to_dev(img), out.t, M, gray=True)
+    torch.cuda.synchronize()
+    out.check()
+    np.testing.assert_array_equal(out.np(), oracle.warp_u8(img, M, H, W, gray=True))
+
+
+@pytest.mark.parametrize("layout", ["hwc", "chw"])
+@pytest.mark.parametrize("H,W,seed", [(1080, 1920, 13), (71, 90, 4)])
+def test_warp_f32(H, W, seed, layout):
+    img = inputs.noise_gradient_image(seed, H, W)
+    M = inputs.warp_matrix(seed, H, W)
+    shape = (H, W, 3) if layout == "hwc" else (3, H, W)
+    out = Guarded(shape, torch.float32)
+    kr.kr_warp_affine(to_dev(img), out.t, M, mean=MEAN, std=STD, dst_layout=layout)
+    g = Guarded((H, W, 1), torch.float32)
+    kr.kr_warp_affine(to_dev(img), g.t, M, gray=True)
+    torch.cuda.synchronize()
+    out.check()
+    g.check()
+    got = out.np() if layout == "hwc" else out.np().transpose(1, 2, 0)
+    assert np.abs(got - oracle.warp_f64(img, M, H, W, mean=MEAN, std=STD)).max() <= F32_TOL
+    assert np.abs(g.np() - oracle.warp_f64(img, M, H, W, gray=True)).max() <= F32_TOL
+
+
+def _special_matrices(H, W):
+    return {
+        "identity": [[1, 0, 0], [0, 1, 0]],
+        "hflip": [[-1, 0, W], [0, 1, 0]],
+        "shift": [[1, 0, 3], [0, 1, -2]],
+        "half_shift": [[1, 0, 0.5], [0, 1, -0.25]],
+        "far_away": [[1, 0, 1e5], [0, 1, 0]],
+        "huge": [[1, 0, 5e6], [0, 1, 5e6]],
+        "zoom_in_x8": [[0.125, 0, 3.3], [0, 0.125, 2.1]],
+        "zoom_out_x9": [[9.1, 0.3, -40], [-0.2, 8.7, -33]],
+        "shear": [[1, 0.7, -20], [0.1, 1, 0]],
+        "degenerate_row": [[0, 0, 10.5], [0, 0, 5.25]],
+        "negative_frac": [[1, 0, -0.3], [0, 1, -0.7]],
+    }
+
+
+@pytest.mark.parametrize("name", list(_special_matrices(1, 1)))
+def test_warp_special_matrices(name):
+    H, W = 67, 93
+    img = inputs.uniform_image(21, H, W, 3)
+    M = np.array(_special_matrices(H, W)[name], np.float32)
+    out = Guarded((H, W, 3), torch.uint8)
+    kr.kr_warp_affine(to_dev(img), out.t, M)
+    f = Guarded((H, W, 3), torch.float32)
+    kr.kr_warp_affine(to_dev(img), f.t, M)
+    torch.cuda.synchronize()
+    out.check()
+    f.check()
+    np.testing.assert_array_equal(out.np(), oracle.warp_u8(img, M, H, W))
+    assert np.abs(f.np() - oracle.warp_f64(img, M, H, W)).max() <= F32_TOL
+    if name == "identity":
+        np.testing.assert_array_equal(out.np(), img)
+    if name == "hflip":
+        np.testing.assert_array_equal(out.np(), img[:, ::-1])
+
+
+def test_warp_output_size_differs_from_source():
+    img = inputs.uniform_image(2, 150, 260, 3)
+    rng = np.random.default_rng(9)
+    M = inputs.random_inverse_affine(rng, 150, 260, 333, 95, k=1.7)
+    out = Guarded((333, 95, 3), torch.uint8)
+    kr.kr_warp_affine(to_dev(img), out.t, M)
+    torch.cuda.synchronize()
+    out.check()
+    np.testing.assert_array_equal(out.np(), oracle.warp_u8(img, M, 333, 95))
+
+
+# ---------------------------------------------------------------------------
+# Views, pitches and batches
+# ---------------------------------------------------------------------------
+def test_views_with_odd_pitch_and_offset():
+    H, W = 83, 129
+    img = inputs.uniform_image(31, H, W, 3)
+    big = torch.full((H + 5, W + 3, 3), 7, dtype=torch.uint8, device=dev())
+    big[2:2 + H, 1:1 + W] = to_dev(img)
+    src = big[2:2 + H, 1:1 + W]                          # pitch (W+3)*3 = 396, offset 2*396 + 3
+    dbig = torch.full((60, 77, 3), CANARY_U8, dtype=torch.uint8, device=dev())
+    dst = dbig[3:3 + 51, 5:5 + 70]                       # odd offset, pitch 231
+    kr.kr_resize_bilinear(src, dst)
+    M = inputs.warp_matrix(31, H, W)
+    wbig = torch.full((H + 2, W + 1, 3), CANARY_U8, dtype=torch.uint8, device=dev())
+    wdst = wbig[1:1 + H, 1:1 + W]
+    kr.kr_warp_affine(src, wdst, M)
+    gbig = torch.full((H + 3, W + 5), CANARY_U8, dtype=torch.uint8, device=dev())
+    gdst = gbig[1:1 + H, 3:3 + W]
+    kr.kr_rgb_to_gray(src, gdst)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(dst.cpu().numpy(), oracle.resize_u8(img, 51, 70))
+    np.testing.assert_array_equal(wdst.cpu().numpy(), oracle.warp_u8(img, M, H, W))
+    np.testing.assert_array_equal(gdst.cpu().numpy()[..., None], oracle.rgb_to_gray_u8(img))
+    for b, sl in ((dbig, (slice(3, 54), slice(5, 75))), (wbig, (slice(1, 1 + H), slice(1, 1 + W))),
+                  (gbig, (slice(1, 1 + H), slice(3, 3 + W)))):
+        m = torch.ones(b.shape[:2], dtype=torch.bool, device=dev())
+        m[sl] = False
+        assert bool((b[m] == CANARY_U8).all()), "write outside the destination view"
+
+
+def test_batch_dimension_one_call():
+    n, H, W, h, w = 5, 61, 97, 40, 130
+    imgs = np.stack([inputs.noise_gradient_image(40 + i, H, W) for i in range(n)])
+    Ms = inputs.warp_matrices(40, n, H, W)
+    src = to_dev(imgs)
+    r = Guarded((n, h, w, 3), torch.uint8)
+    kr.kr_resize_bilinear(src, r.t)
+    wu = Guarded((n, H, W, 3), torch.uint8)
+    kr.kr_warp_affine(src, wu.t, Ms)
+    wf = Guarded((n, 3, H, W), torch.float32)
+    kr.kr_warp_affine(src, wf.t, Ms, mean=MEAN, std=STD, dst_layout="chw")
+    torch.cuda.synchronize()
+    for g in (r, wu, wf):
+        g.check()
+    for i in range(n):
+        np.testing.assert_array_equal(r.np()[i], oracle.resize_u8(imgs[i], h, w))
+        np.testing.assert_array_equal(wu.np()[i], oracle.warp_u8(imgs[i], Ms[i], H, W))
+        ref = oracle.warp_f64(imgs[i], Ms[i], H, W, mean=MEAN, std=STD)
+        assert np.abs(wf.np()[i].transpose(1, 2, 0) - ref).max() <= F32_TOL
+
+
+def test_warp_batch_over_one_launch_limit():
+    # more images than one launch carries matrices for: the library splits launches
+    n, H, W = 130, 20, 24
+    imgs = inputs.uniform_batch(5, n, H, W, 3)
+    Ms = inputs.warp_matrices(5, n, H, W)
+    out = Guarded((n, H, W, 3), torch.uint8)
+    kr.kr_warp_affine(to_dev(imgs), out.t, Ms)
+    torch.cuda.synchronize()
+    out.check()
+    got = out.np()
+    for i in (0, 1, 127, 128, 129):
+        np.testing.assert_array_equal(got[i], oracle.warp_u8(imgs[i], Ms[i], H, W))
+
+
+@pytest.mark.parametrize("H,W", [(1080, 1920), (7, 13), (33, 16), (5, 47)])
+def test_rgb_to_gray(H, W):
+    img = inputs.uniform_image(H + W, H, W, 3)
+    out = Guarded((H, W, 1), torch.uint8)
+    kr.kr_rgb_to_gray(to_dev(img), out.t)
+    torch.cuda.synchronize()
+    out.check()
+    np.testing.assert_array_equal(out.np(), oracle.rgb_to_gray_u8(img))
+
+
+def test_errors_do_not_enqueue():
+    src = torch.zeros((10, 10, 3), dtype=torch.uint8, device=dev())
+    dst = torch.zeros((5, 5, 1), dtype=torch.uint8, device=dev())
+    with pytest.raises(kr.KrError) as e:
+        kr.kr_resize_bilinear(src, dst)           # channel mismatch without gray
+    assert e.value.status == 1
+    with pytest.raises(kr.KrError) as e:
+        kr.kr_resize_bilinear(src, src[:5, :5])   # overlapping destination
+    assert e.value.status == 3
+    with pytest.raises(kr.KrError):
+        kr.kr_warp_affine(src, src.clone(), [np.nan, 0, 0, 0, 1, 0])
