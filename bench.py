@@ -1,0 +1,483 @@
+"""Benchmark of the resampling path on GB300.
+
+One step = every operation of the path over a batch of 32 synthetic 1920x1080x3
+u8 video frames (inputs larger than L2: 199 MB of sources per step), each
+operation one launch over the whole batch through the C ABI:
+
+  resize -> 1280x720: u8 | u8 + fused gray | f32 | f32 + normalise, planar CHW
+  warp_affine -> 1920x1080 (per-frame inverse map): u8 | u8 + fused gray | f32
+  rgb_to_gray (standalone)
+
+Metric: output Gpixel/s of the whole step (all ranks), plus the HBM roofline of
+the dominant kernel (algorithmic bytes = output bytes + unique source bytes
+read, from tests/golden/bench_touched.json, over its CUDA-event duration), the
+oracle timed on the host cores, the end-to-end rate through the public API
+with pinned host buffers, a ragged-batch comparison (256 warps in one
+persistent graph-replayed launch vs 256 per-image launches) and SM clocks
+sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gb300,reference}]
+
+Under torchrun each rank runs its own copy of the workload (weak scaling); the
+step time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2505_12425_gb300 import inputs  # noqa: E402
+
+METRIC = "Gpixel/s and HBM GB/s %peak for resize/warp; p50/p99 latency batched vs per-image"
+UNIT = "Gpixel/s"
+WORKLOAD = "32 x 1920x1080x3 u8 frames: resize->1280x720 (u8, u8+gray, f32, f32 norm CHW), " \
+           "warp_affine->1920x1080 (u8, u8+gray, f32), rgb_to_gray"
+MEAN, STD = inputs.IMAGENET_MEAN, inputs.IMAGENET_STD
+RS_H, RS_W = 720, 1280
+
+
+def op_table():
+    """(name, output pixels per image, output bytes per image) of the step's operations."""
+    H, W = inputs.BENCH_H, inputs.BENCH_W
+    r, w = RS_H * RS_W, H * W
+    return [
+        ("resize_u8", r, 3 * r), ("resize_gray_u8", r, r), ("resize_f32", r, 12 * r),
+        ("resize_norm_f32_chw", r, 12 * r), ("warp_u8", w, 3 * w), ("warp_gray_u8", w, w),
+        ("warp_f32", w, 12 * w), ("rgb_to_gray", w, w),
+    ]
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2505_12425_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def load_traffic(op):
+    """ncu dram bytes per launch of `op`, if captured from the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get("per_op", {}).get(op)
+    if not e or d.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling (nvidia-smi) during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        self.idx = gpu_index
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return None
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        mx = float(rows[0][2])
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, v in zip(names, r[5:9]):
+                if v.strip() == "Active":
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].strip()[:1].isdigit())
+                if any(r[3].strip()[:1].isdigit() for r in rows) else None}
+
+
+# ---------------------------------------------------------------------------
+# The GPU arm
+# ---------------------------------------------------------------------------
+class Step:
+    """Prepared C-ABI calls of one step (descriptors built once)."""
+
+    def __init__(self, torch, kr, dev, imgs_dev, Ms):
+        self.torch, self.kr = torch, kr
+        n, H, W = imgs_dev.shape[0], inputs.BENCH_H, inputs.BENCH_W
+        e = lambda *s, dt=torch.uint8: torch.empty(*s, dtype=dt, device=dev)  # noqa: E731
+        f32 = torch.float32
+        self.src = imgs_dev
+        self.outs = {
+            "resize_u8": e((n, RS_H, RS_W, 3)), "resize_gray_u8": e((n, RS_H, RS_W, 1)),
+            "resize_f32": e((n, RS_H, RS_W, 3), dt=f32), "resize_norm_f32_chw": e((n, 3, RS_H, RS_W), dt=f32),
+            "warp_u8": e((n, H, W, 3)), "warp_gray_u8": e((n, H, W, 1)), "warp_f32": e((n, H, W, 3), dt=f32),
+            "rgb_to_gray": e((n, H, W, 1)),
+        }
+        lib = kr.load()
+        self.lib = lib
+        self.Ms = np.ascontiguousarray(Ms.reshape(-1), dtype=np.float32)
+        self.Mp = self.Ms.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        s = kr.image(imgs_dev)
+        self._keep = []
+
+        def call_resize(name, layout="hwc", **p):
+            d, pp = kr.image(self.outs[name], layout), kr.post(**p)
+            self._keep += [d, pp]
+            return lambda st: lib.kr_resize_bilinear(ctypes.byref(s), ctypes.byref(d), ctypes.byref(pp), st)
+
+        def call_warp(name, **p):
+            d, pp = kr.image(self.outs[name]), kr.post(**p)
+            self._keep += [d, pp]
+            return lambda st: lib.kr_warp_affine(ctypes.byref(s), ctypes.byref(d), self.Mp, ctypes.byref(pp), st)
+
+        def call_gray(name):
+            d = kr.image(self.outs[name])
+            self._keep.append(d)
+            return lambda st: lib.kr_rgb_to_gray(ctypes.byref(s), ctypes.byref(d), st)
+
+        self._keep.append(s)
+        self.calls = [
+            ("resize_u8", call_resize("resize_u8")),
+            ("resize_gray_u8", call_resize("resize_gray_u8", gray=True)),
+            ("resize_f32", call_resize("resize_f32")),
+            ("resize_norm_f32_chw", call_resize("resize_norm_f32_chw", "chw", mean=MEAN, std=STD)),
+            ("warp_u8", call_warp("warp_u8")),
+            ("warp_gray_u8", call_warp("warp_gray_u8", gray=True)),
+            ("warp_f32", call_warp("warp_f32")),
+            ("rgb_to_gray", call_gray("rgb_to_gray")),
+        ]
+
+    def run(self, stream_handle, events=None):
+        for i, (name, c) in enumerate(self.calls):
+            if events is not None:
+                events[i][0].record()
+            st = c(stream_handle)
+            if st != 0:
+                raise RuntimeError(f"{name}: status {st} {self.lib.kr_last_error().decode()}")
+            if events is not None:
+                events[i][1].record()
+
+
+def ragged_compare(torch, kr, dev, reps=20):
+    """256 warps (sides log-uniform 64..2048, output 0.25-2x): one persistent graph-replayed
+    launch vs 256 per-image launches. Returns a summary dict."""
+    spec = inputs.ragged_batch(1003, 256)
+    srcs, dsts, work = [], [], []
+    for it in spec:
+        s = torch.from_numpy(inputs.uniform_image(it.seed, it.H, it.W, 3)).to(dev)
+        d = torch.empty((it.h, it.w, 3), dtype=torch.uint8, device=dev)
+        srcs.append(s)
+        dsts.append(d)
+        work.append(kr.work_item(kr.KR_OP_WARP, s, d, M=it.M))
+    arr = kr.work_array(work)
+    ws = torch.empty(kr.kr_batch_workspace_size(len(arr)), dtype=torch.uint8, device=dev)
+    cfg, ctas = kr.kr_autotune_batch(arr, ws)
+    out_px = sum(it.h * it.w for it in spec)
+    lib = kr.load()
+    single = []
+    for it, s, d in zip(spec, srcs, dsts):
+        si, di, pp = kr.image(s), kr.image(d), kr.post()
+        M = np.ascontiguousarray(it.M.reshape(-1), dtype=np.float32)
+        single.append((si, di, pp, M, M.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    opts = kr.KrBatchOpts(-1, 0, 1)
+
+    def batched():
+        r = lib.kr_batch_submit(arr, len(arr), ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.byref(opts), st)
+        assert r == 0, r
+
+    def per_image():
+        for si, di, pp, _, Mp in single:
+            r = lib.kr_warp_affine(ctypes.byref(si), ctypes.byref(di), Mp, ctypes.byref(pp), st)
+            assert r == 0, r
+
+    res = {}
+    for name, fn in (("batched", batched), ("per_image", per_image)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            times.append(a.elapsed_time(b))
+        times.sort()
+        res[name] = {"ms_p50": round(statistics.median(times), 4),
+                     "ms_p99": round(times[min(len(times) - 1, int(0.99 * len(times)))], 4),
+                     "gpx_s": round(out_px / (statistics.median(times) * 1e-3) / 1e9, 3)}
+    res.update({"items": 256, "out_px": out_px, "tile_config": list(kr.kr_tile_config_shape(cfg)),
+                "ctas_per_sm": ctas, "launches_batched": 1, "launches_per_image": 256,
+                "speedup_p50": round(res["per_image"]["ms_p50"] / res["batched"]["ms_p50"], 3)})
+    return res
+
+
+def cpu_baseline_sample(budget_s=12.0):
+    """The oracle (single-threaded C) on a bounded sample of the step: whole frames, all eight
+    operations, until the time budget is spent."""
+    import oracle
+    imgs_n = inputs.BENCH_IMAGES
+    Ms = inputs.bench_matrices(imgs_n)
+    H, W = inputs.BENCH_H, inputs.BENCH_W
+    px_per_img = sum(p for _, p, _ in op_table())
+    done, t_total = 0, 0.0
+    for i in range(imgs_n):
+        img = inputs.noise_gradient_image(2000 + i, H, W)
+        t0 = time.perf_counter()
+        oracle.resize_u8(img, RS_H, RS_W)
+        oracle.resize_u8(img, RS_H, RS_W, gray=True)
+        oracle.resize_f64(img, RS_H, RS_W)
+        oracle.resize_f64(img, RS_H, RS_W, mean=MEAN, std=STD)
+        oracle.warp_u8(img, Ms[i], H, W)
+        oracle.warp_u8(img, Ms[i], H, W, gray=True)
+        oracle.warp_f64(img, Ms[i], H, W)
+        oracle.rgb_to_gray_u8(img)
+        t_total += time.perf_counter() - t0
+        done += 1
+        if t_total >= budget_s:
+            break
+    return {"value": round(done * px_per_img / t_total / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{done} of {imgs_n} frames, all 8 operations, single-threaded C oracle "
+                      f"({t_total:.1f} s)"}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__ as ge
+    from paper_2505_12425_gb300 import binding as kr
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        ge.build()
+    if world > 1:
+        dist.barrier()
+    kr.load()
+
+    n = args.images
+    imgs = inputs.bench_images(n)
+    Ms = inputs.bench_matrices(n)
+    imgs_dev = torch.from_numpy(imgs).to(dev)
+    step = Step(torch, kr, dev, imgs_dev, Ms)
+    stream = torch.cuda.current_stream()
+    sh = ctypes.c_void_p(stream.cuda_stream)
+    ops = op_table()
+
+    for _ in range(args.warmup):
+        step.run(sh)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    events = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in ops]
+              for _ in range(K)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t_start.record()
+        for k in range(K):
+            step.run(sh, events[k])
+        t_end.record()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms_total = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / K
+    px_step = n * sum(p for _, p, _ in ops)
+    value = world * px_step / (ms_step * 1e-3) / 1e9
+
+    # per-operation kernel times (each call is one launch for this batch size)
+    per_op = {}
+    for i, (name, px, ob) in enumerate(ops):
+        d = [events[k][i][0].elapsed_time(events[k][i][1]) for k in range(K)]
+        per_op[name] = statistics.mean(d)
+    touched = json.load(open(os.path.join(ROOT, "tests", "golden", "bench_touched.json")))["per_op"]
+    dominant = max(per_op, key=per_op.get)
+    peak, peak_kind = load_peaks()
+    breakdown = {}
+    for name, px, ob in ops:
+        alg = n * ob + sum(touched[name]["touched_bytes"][:n])
+        gbs = alg / (per_op[name] * 1e-3) / 1e9
+        breakdown[name] = {"ms": round(per_op[name], 4), "alg_bytes": alg, "GB_s": round(gbs, 1),
+                           "frac_of_measured_hbm": round(gbs / peak, 3),
+                           "share": round(per_op[name] / sum(per_op.values()), 3)}
+    dom = breakdown[dominant]
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": dom["GB_s"], "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": dom["frac_of_measured_hbm"],
+                "traffic": load_traffic(dominant), "alg_bytes_per_launch": dom["alg_bytes"]}
+
+    # end to end through the public API: pinned H2D of the inputs, the step, D2H of every output
+    host_in = torch.from_numpy(imgs).pin_memory()
+    host_out = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in step.outs.items()}
+    h2d = host_in.numel()
+    d2h = sum(v.numel() * v.element_size() for v in host_out.values())
+    K_e2e = max(3, min(K, 20))
+    for _ in range(2):
+        imgs_dev.copy_(host_in, non_blocking=True)
+        step.run(sh)
+        for k, v in step.outs.items():
+            host_out[k].copy_(v, non_blocking=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K_e2e):
+        imgs_dev.copy_(host_in, non_blocking=True)
+        step.run(sh)
+        for k, v in step.outs.items():
+            host_out[k].copy_(v, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / K_e2e
+    if world > 1:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = {"value": round(world * px_step / (ms_e2e * 1e-3) / 1e9, 3), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 3),
+           "steps": K_e2e}
+
+    ragged = ragged_compare(torch, kr, dev) if not args.no_extras else None
+    cpu = cpu_baseline_sample() if (rank == 0 and not args.no_extras) else None
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8 (int32 fixed-point) + f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if n == inputs.BENCH_IMAGES else WORKLOAD.replace("32 x", f"{n} x"),
+                       "images_per_step": n, "out_px_per_step": px_step,
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "l2": "no flush: 199 MB of distinct source frames per step > 129 MB L2"},
+            "roofline": roofline, "per_op": breakdown, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": K * len(ops), "ragged": ragged, "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is a bounded sample of the workload (one frame,
+    all eight operations) on the host cores."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    Ms = inputs.bench_matrices(inputs.BENCH_IMAGES)
+    H, W = inputs.BENCH_H, inputs.BENCH_W
+    px = sum(p for _, p, _ in op_table())
+    frames = [inputs.noise_gradient_image(2000 + i, H, W) for i in range(min(4, inputs.BENCH_IMAGES))]
+
+    def one(i):
+        img, M = frames[i % len(frames)], Ms[i % len(frames)]
+        oracle.resize_u8(img, RS_H, RS_W)
+        oracle.resize_u8(img, RS_H, RS_W, gray=True)
+        oracle.resize_f64(img, RS_H, RS_W)
+        oracle.resize_f64(img, RS_H, RS_W, mean=MEAN, std=STD)
+        oracle.warp_u8(img, M, H, W)
+        oracle.warp_u8(img, M, H, W, gray=True)
+        oracle.warp_f64(img, M, H, W)
+        oracle.rgb_to_gray_u8(img)
+
+    for i in range(args.warmup):
+        one(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        one(i)
+    dt = time.perf_counter() - t0
+    value = args.steps * px / dt / 1e9
+    sample = f"each step: 1 of {inputs.BENCH_IMAGES} frames, all 8 operations, single-threaded C oracle"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64 fixed-point + f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "images_per_step": 1},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-extras", action="store_true", help="skip the ragged comparison and the CPU baseline")
+    ap.add_argument("--images", type=int, default=inputs.BENCH_IMAGES,
+                    help="frames per step (the full workload is 32; fewer only for small profiling cases)")
+    args = ap.parse_args()
+    if not 1 <= args.images <= inputs.BENCH_IMAGES:
+        ap.error(f"--images must be in 1..{inputs.BENCH_IMAGES}")
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -196,12 +196,6 @@ def touched_bytes(bitmap, C, row_bytes=None, sector=None):
         return int(bm.sum()) * C
     H, W = bm.shape
     row_bytes = W * C if row_bytes is None else row_bytes
-    total = 0
-    for y in range(H):
-        xs = np.nonzero(bm[y])[0]
-        if xs.size == 0:
-            continue
-        first = (y * row_bytes + xs * C) // sector
-        last = (y * row_bytes + xs * C + C - 1) // sector
-        total += np.unique(np.concatenate([first, last])).size
-    return total * sector
+    ys, xs = np.nonzero(bm)
+    off = ys.astype(np.int64) * row_bytes + xs.astype(np.int64) * C
+    return int(np.unique(np.concatenate([off // sector, (off + C - 1) // sector])).size) * sector

@@ -9,9 +9,10 @@ tests) share.
 Recipes (numpy ``default_rng(seed)``, PCG64, identical on x86-64 and aarch64):
 
 * uniform images: i.i.d. uniform integers 0..255 per channel;
-* noise + gradient images: ``round(0.5 * noise + 0.5 * 255 * g_c)``, where
+* noise + gradient images: ``(noise + round(255 * g_c) + 1) // 2`` (the mean
+  of uniform noise and a smooth gradient, rounded half up), where
   ``g(x, y) = (x / (W - 1) + y / (H - 1)) / 2`` and channel c is shifted by
-  c/3 modulo 1, clipped to 0..255;
+  c/3 modulo 1;
 * affine maps: rotation U(-30 deg, 30 deg), scale U(0.8, 1.2), translation
   U(-100, 100) px on each axis, about the image centre. The forward map
   A = T(c_dst + t) R(theta) S(s) T(-c_src) is built and inverted in float64,
@@ -25,6 +26,7 @@ Recipes (numpy ``default_rng(seed)``, PCG64, identical on x86-64 and aarch64):
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass
 
@@ -49,15 +51,18 @@ def uniform_batch(seed: int, n: int, H: int, W: int, C: int = 3) -> np.ndarray:
     return rng.integers(0, 256, size=(n, H, W, C), dtype=np.uint8)
 
 
-def noise_gradient_image(seed: int, H: int, W: int, C: int = 3) -> np.ndarray:
-    rng = np.random.default_rng(seed)
-    noise = rng.integers(0, 256, size=(H, W, C)).astype(np.float64)
+@functools.lru_cache(maxsize=4)
+def _gradient(H: int, W: int, C: int) -> np.ndarray:
     gx = np.arange(W, dtype=np.float64) / max(W - 1, 1)
     gy = np.arange(H, dtype=np.float64) / max(H - 1, 1)
     g = (gx[None, :] + gy[:, None]) / 2.0
-    grad = np.stack([np.mod(g + c / 3.0, 1.0) for c in range(C)], axis=-1) * 255.0
-    img = np.rint(0.5 * noise + 0.5 * grad)
-    return np.clip(img, 0, 255).astype(np.uint8)
+    return np.stack([np.rint(np.mod(g + c / 3.0, 1.0) * 255.0) for c in range(C)], axis=-1).astype(np.uint16)
+
+
+def noise_gradient_image(seed: int, H: int, W: int, C: int = 3) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    noise = rng.integers(0, 256, size=(H, W, C), dtype=np.uint8).astype(np.uint16)
+    return ((noise + _gradient(H, W, C) + 1) >> 1).astype(np.uint8)
 
 
 def _forward_affine(theta, s, tx, ty, c_src, c_dst):
@@ -90,6 +95,21 @@ def warp_matrix(seed: int, H: int, W: int) -> np.ndarray:
 def warp_matrices(seed: int, n: int, H: int, W: int) -> np.ndarray:
     rng = np.random.default_rng(seed)
     return np.stack([random_inverse_affine(rng, H, W) for _ in range(n)])
+
+
+# The 1920x1080 video-frame workload of the benchmark: BENCH_IMAGES noise +
+# gradient frames (seeds 2000 + i), each with its own inverse affine map
+# (seeds 3000 + i: rotation +-30 deg, scale 0.8-1.2, translation +-100 px).
+BENCH_IMAGES = 32
+BENCH_H, BENCH_W = 1080, 1920
+
+
+def bench_images(n: int = BENCH_IMAGES) -> np.ndarray:
+    return np.stack([noise_gradient_image(2000 + i, BENCH_H, BENCH_W) for i in range(n)])
+
+
+def bench_matrices(n: int = BENCH_IMAGES) -> np.ndarray:
+    return np.stack([warp_matrix(3000 + i, BENCH_H, BENCH_W) for i in range(n)])
 
 
 @dataclass
