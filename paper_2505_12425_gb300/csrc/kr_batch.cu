@@ -38,10 +38,11 @@ struct alignas(16) WorkItem {
     int32_t kind;          // KIND_* below
     int32_t tiles_x;
     int32_t foot_budget;
+    int32_t region_b;
     int32_t chw;
+    int32_t allow_fast;
     float M[6];
     float scale[3], bias[3];
-    int32_t pad[2];
 };
 static_assert(sizeof(WorkItem) == 128, "work item is 128 bytes");
 
@@ -86,6 +87,8 @@ __device__ __forceinline__ Job job_of(const WorkItem &it)
     J.w = it.w;
     J.chw = it.chw;
     J.foot_budget = it.foot_budget;
+    J.region_b = it.region_b;
+    J.allow_fast = it.allow_fast;
 #pragma unroll
     for (int k = 0; k < 6; ++k) J.M[k] = it.M[k];
 #pragma unroll
@@ -155,13 +158,16 @@ struct TileCfg {
     int max_smem;
 };
 
-template <int TW, int TH> static constexpr int max_out_stage() { return 3 * TH * round16(TW * 4 + 15); }
+template <int TW, int TH> static constexpr int max_region_b()
+{
+    return 3 * TH * round16(TW * 4 + 15) > kRegionBCap ? 3 * TH * round16(TW * 4 + 15) : kRegionBCap;
+}
 
 static TileCfg g_cfgs[] = {
-    {64, 32, (const void *)ragged_kernel<64, 32>, kFootCap + max_out_stage<64, 32>()},
-    {32, 32, (const void *)ragged_kernel<32, 32>, kFootCap + max_out_stage<32, 32>()},
-    {128, 16, (const void *)ragged_kernel<128, 16>, kFootCap + max_out_stage<128, 16>()},
-    {64, 16, (const void *)ragged_kernel<64, 16>, kFootCap + max_out_stage<64, 16>()},
+    {64, 32, (const void *)ragged_kernel<64, 32>, kFootCap + max_region_b<64, 32>()},
+    {32, 32, (const void *)ragged_kernel<32, 32>, kFootCap + max_region_b<32, 32>()},
+    {128, 16, (const void *)ragged_kernel<128, 16>, kFootCap + max_region_b<128, 16>()},
+    {64, 16, (const void *)ragged_kernel<64, 16>, kFootCap + max_region_b<64, 16>()},
 };
 constexpr int kNumCfgs = sizeof(g_cfgs) / sizeof(g_cfgs[0]);
 
@@ -219,9 +225,13 @@ static kr_status pack_items(const kr_work_t *items, int n, int tw, int th, Packe
             it.kind = kind_of(op, d.cin, d.outk);
             for (int k = 0; k < 6; ++k) it.M[k] = op == OP_WARP ? w.M[k] : 0.f;
             for (int k = 0; k < 3; ++k) { it.scale[k] = d.scale[k]; it.bias[k] = d.bias[k]; }
-            it.foot_budget = op == OP_RESIZE ? foot_budget_resize(d.cin, d.H, d.W, d.h, d.w, tw, th)
-                                             : foot_budget_warp(d.cin, d.H, d.W, it.M, tw, th);
-            P.smem = std::max(P.smem, (size_t)it.foot_budget + out_stage_of(d.outk, d.cin, tw, th));
+            const int ob = out_stage_of(d.outk, d.cin, tw, th);
+            const Budget bud = op == OP_RESIZE ? budget_resize(d.cin, d.H, d.W, d.h, d.w, tw, th, ob)
+                                               : budget_warp(d.cin, d.H, d.W, it.M, tw, th, ob);
+            it.foot_budget = bud.a;
+            it.region_b = bud.b;
+            it.allow_fast = op == OP_RESIZE ? 1 : (warp_allows_fast(it.M, d.h, d.w) ? 1 : 0);
+            P.smem = std::max(P.smem, (size_t)bud.a + bud.b);
         } else {
             return KR_ERR_INVALID_ARG;
         }
@@ -327,7 +337,7 @@ static cudaError_t prepare_cfg(int cfg, size_t smem, int &occ)
 
 static std::string class_key(const Packed &P, int n)
 {
-    char b[160];
+    char b[320];
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceProp prop;

@@ -1,20 +1,32 @@
 // Device-side tile engine of the resampling kernels (sm_103a).
 //
 // One CTA of kThreads threads produces one TW x TH tile of output pixels:
-//   1. the source footprint of the tile (the bounding box of every tap) is
-//      copied into shared memory: 16-byte cp.async for the aligned body of
-//      each source row, byte loads for its unaligned head and tail;
-//   2. every output pixel takes its four taps from shared memory (global
-//      memory at the zero border, or when the footprint does not fit) and
-//      blends them: u8 with 11-bit weights through dp2a, f32 with fp32 FMAs;
-//   3. results are written into a shared-memory copy of the output tile whose
-//      rows carry the same 16-byte phase as their global rows, so the tile
-//      leaves through 128-bit coalesced stores (byte stores only for the
-//      unaligned head and tail of a row).
+//   1. plan: the source box of the tile (the bounding box of every tap, from
+//      the resize axis tables or from the warp map at the tile corners) and a
+//      per-tile "fast" flag;
+//   2. stage: the box's source rows are copied into shared memory as whole
+//      16-byte chunks with cp.async; 3-channel rows are then re-laid out as one
+//      32-bit word per pixel (R, G, B, pad) so that every tap is one aligned
+//      32-bit shared load;
+//   3. compute: fast tiles (every tap inside the box, coordinates in the range
+//      where the cheap weight form is exact) run a branch-free pixel loop; other
+//      tiles (image border, huge or non-finite coordinates, boxes too large for
+//      shared memory) take the general per-pixel path, which reads taps from
+//      the box when they are inside it and from global memory (zero outside the
+//      image) otherwise;
+//   4. write-out: results go into a shared copy of the output tile whose rows
+//      keep the 16-byte phase of their global rows, then leave through 128-bit
+//      coalesced stores (head and tail bytes one per lane).
 //
-// The arithmetic follows the definitions stated in include/kr.h (half-pixel
-// centres, clamp-to-edge resize, zero-border warp with the fixed fp32
-// coordinate sequence, 11-bit round-half-up weights, BT.601 gray).
+// Arithmetic (definitions shared with the C ABI documentation):
+//   resize   sx = (x + 1/2) W / w - 1/2 as the exact rational num/den, clamp to
+//            the edge; 11-bit weight of the second tap rounded half up;
+//   warp     sx = fmaf(m00, x + 1/2, fmaf(m01, y + 1/2, m02)) - 1/2 in fp32,
+//            taps floor(sx), floor(sx) + 1, zero outside the image, 11-bit
+//            weight = round-half-up of 2048 * (sx - floor(sx));
+//   u8       out = (v + 2^21) >> 22, v = sum of tap * wx * wy (exact integers);
+//   f32      p/255 blended with fp32 weights, then * scale[c] + bias[c];
+//   gray     (4899 R + 9617 G + 1868 B + 8192) >> 14 (u8), 0.299/0.587/0.114 (f32).
 #pragma once
 
 #include <cstdint>
@@ -38,13 +50,16 @@ struct Job {
     int64_t dplane;       // CHW plane stride in bytes
     int32_t h, w;
     int32_t chw;          // f32 planar destination
-    int32_t foot_budget;  // shared bytes available for the source footprint (0: never stage)
+    int32_t foot_budget;  // shared bytes of region A (staged box); 0 = never stage
+    int32_t region_b;     // shared bytes of region B (raw rows of 3-channel boxes, then output tile)
+    int32_t allow_fast;   // warp: the map's intermediate terms are small enough for the fast path
     float M[6];           // destination -> source map (warp)
     float scale[3];       // f32: out = v255 * scale[c] + bias[c]
     float bias[3];
 };
 
 __host__ __device__ constexpr int round16(int x) { return (x + 15) & ~15; }
+__host__ __device__ constexpr int round4(int x) { return (x + 3) & ~3; }
 
 // Bytes per output element and channels of the destination.
 template <int OUTK, int CIN> struct OutTraits {
@@ -64,6 +79,16 @@ __host__ __device__ constexpr int out_stage_bytes()
                ? OutTraits<OUTK, CIN>::dC * TH * round16(TW * 4 + 15)
                : TH * round16(TW * OutTraits<OUTK, CIN>::dC + 15);
 }
+
+// Staged-box geometry of a box `cols` source pixels wide.
+//   raw row:  the row's bytes as whole 16-byte chunks, with room for the 16-byte
+//             phase and for the last 4-pixel group of the re-layout;
+//   word row: one 32-bit word per pixel plus one spare, a multiple of 4 words.
+__host__ __device__ constexpr int raw_row_bytes(int cols, int cin)
+{
+    return cin == 3 ? round16(15 + 12 * ((cols + 3) / 4) + 4) : round16(cols + 15 + 2);
+}
+__host__ __device__ constexpr int word_row(int cols) { return round4(cols + 1); }
 
 // ---------------------------------------------------------------------------
 // Coordinate maps
@@ -131,6 +156,14 @@ __device__ __forceinline__ void warp_weight(float s, int &i0, int &q)
     q = (int)k + (__fsub_rn(t, k) >= 0.5f ? 1 : 0);
 }
 
+// Fast form of warp_weight for a = s + 1/2 with s in [0, 4094): T = floor(2048 a - 1023.5)
+// computed with one rounding equals 2048 * floor(s) + q exactly (every fp32 value of the
+// range is checked on the host). q = 2048 comes out as (floor(s) + 1, 0): the same sample.
+__device__ __forceinline__ int warp_fixed_fast(float a)
+{
+    return __float2int_rd(__fmaf_rn(a, 2048.f, -1023.5f));
+}
+
 // ---------------------------------------------------------------------------
 // Small helpers
 // ---------------------------------------------------------------------------
@@ -150,18 +183,7 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Six bytes starting at shared byte offset o (two RGB pixels): lo = bytes 0..3, hi = bytes 4..5.
-__device__ __forceinline__ void lds6(const uint8_t *s, int o, uint32_t &lo, uint32_t &hi)
-{
-    const uint32_t *wp = reinterpret_cast<const uint32_t *>(s + (o & ~3));
-    const uint32_t sh = (uint32_t)(o & 3) * 8u;
-    const uint32_t w0 = wp[0], w1 = wp[1];
-    const uint32_t w2 = (o & 3) > 2 ? wp[2] : 0u;
-    lo = __funnelshift_r(w0, w1, sh);
-    hi = __funnelshift_r(w1, w2, sh);
-}
-
-// One RGB pixel from global memory (zero outside the image).
+// One RGB pixel from global memory as a word R | G << 8 | B << 16 (zero outside the image).
 __device__ __forceinline__ uint32_t ldg_px3(const uint8_t *src, int64_t spitch, int H, int W, int y,
                                             int x)
 {
@@ -184,23 +206,20 @@ __device__ __forceinline__ float byte_f(uint32_t w, int k)
     return __fsub_rn(__uint_as_float(__byte_perm(w, 0x4B000000u, sel)), 8388608.f);
 }
 
-// Byte i (0..7) of the pair (lo, hi) as an exact float; i is a compile-time constant.
-__device__ __forceinline__ float pair_f(uint32_t lo, uint32_t hi, int i)
-{
-    return i < 4 ? byte_f(lo, i) : byte_f(hi, i - 4);
-}
+// Packed 11-bit weight pair for dp2a: low half 2048 - q, high half q.
+__device__ __forceinline__ uint32_t wpair(int q) { return 2048u + (uint32_t)q * 65535u; }
 
-// u8 blend of two rows of RGB tap pairs. lo/hi: bytes R0 G0 B0 R1 | G1 B1 of a row.
+// Horizontal u8 blend of two RGB pixel words a, b (R | G<<8 | B<<16) with weight pair w.
 struct U8x3 { uint32_t r, g, b; };
 
-__device__ __forceinline__ U8x3 hblend3(uint32_t lo, uint32_t hi, uint32_t wx)
+__device__ __forceinline__ U8x3 hblend_px(uint32_t a, uint32_t b, uint32_t w)
 {
-    const uint32_t rg = __byte_perm(lo, hi, 0x4130);   // R0 R1 G0 G1
-    const uint32_t bb = __byte_perm(lo, hi, 0x0052);   // B0 B1
+    const uint32_t rg = __byte_perm(a, b, 0x5140);   // Ra Rb Ga Gb
+    const uint32_t bb = __byte_perm(a, b, 0x0062);   // Ba Bb
     U8x3 o;
-    o.r = __dp2a_lo(wx, rg, 0u);
-    o.g = __dp2a_hi(wx, rg, 0u);
-    o.b = __dp2a_lo(wx, bb, 0u);
+    o.r = __dp2a_lo(w, rg, 0u);
+    o.g = __dp2a_hi(w, rg, 0u);
+    o.b = __dp2a_lo(w, bb, 0u);
     return o;
 }
 
@@ -214,12 +233,16 @@ __device__ __forceinline__ uint32_t gray_u8(uint32_t r, uint32_t g, uint32_t b)
     return (4899u * r + 9617u * g + 1868u * b + 8192u) >> 14;
 }
 
-// Shared tile-level state of the engine: the staged source box and, for
-// resize, the per-column and per-row axis maps of the current tile.
+// ---------------------------------------------------------------------------
+// Shared tile state
+// ---------------------------------------------------------------------------
 struct TileInfo {
     int fx0, fx1, fy0, fy1;   // staged source box (inclusive)
-    int srow;                 // shared bytes per staged row
-    int staged;               // 1 if the footprint is in shared memory
+    int srow;                 // raw bytes per staged row
+    int sw;                   // words per row of the re-laid 3-channel box
+    int staged;               // the box is in shared memory
+    int fast;                 // every tap of the tile is inside the box (and, for warp,
+                              // every coordinate lies in [0, 4094))
 };
 
 template <int TW, int TH> struct TileShared {
@@ -232,6 +255,64 @@ template <int TW, int TH> struct TileShared {
     float rf[TH];
 };
 
+// Where one output row of the tile goes in the shared output copy: the HWC row,
+// or the three CHW plane rows (each keeping the 16-byte phase of its global row).
+struct ORow {
+    uint8_t *p0, *p1, *p2;
+};
+
+// ---------------------------------------------------------------------------
+// Per-pixel output: blend the taps and put the result into the output tile.
+// Taps are words R | G<<8 | B<<16 (3 channels) or the pixel in byte 0 (1 channel).
+// ---------------------------------------------------------------------------
+template <int CIN, int OUTK>
+__device__ __forceinline__ void emit(const Job &J, const ORow &o, int c, uint32_t p00, uint32_t p01,
+                                     uint32_t p10, uint32_t p11, int qx, int qy, float fx, float fy)
+{
+    using OT = OutTraits<OUTK, CIN>;
+    if (!OT::is_f32) {
+        uint8_t *op = o.p0 + c * OT::dC;
+        const uint32_t w = wpair(qx);
+        if (CIN == 3) {
+            const U8x3 a = hblend_px(p00, p01, w), b = hblend_px(p10, p11, w);
+            const uint32_t r = vblend(a.r, b.r, qy), g = vblend(a.g, b.g, qy), bl = vblend(a.b, b.b, qy);
+            if (OUTK == OUT_U8_GRAY) {
+                op[0] = (uint8_t)gray_u8(r, g, bl);
+            } else {
+                op[0] = (uint8_t)r;
+                op[1] = (uint8_t)g;
+                op[2] = (uint8_t)bl;
+            }
+        } else {
+            const uint32_t t = __dp2a_lo(w, __byte_perm(p00, p01, 0x0040), 0u);
+            const uint32_t b = __dp2a_lo(w, __byte_perm(p10, p11, 0x0040), 0u);
+            op[0] = (uint8_t)vblend(t, b, qy);
+        }
+    } else {
+        float v[3];
+#pragma unroll
+        for (int k = 0; k < CIN; ++k) {
+            const float a = byte_f(p00, k), b = byte_f(p01, k);
+            const float cc = byte_f(p10, k), d = byte_f(p11, k);
+            const float h0 = __fmaf_rn(fx, __fsub_rn(b, a), a);
+            const float h1 = __fmaf_rn(fx, __fsub_rn(d, cc), cc);
+            v[k] = __fmaf_rn(fy, __fsub_rn(h1, h0), h0);
+        }
+        if (OUTK == OUT_F32_GRAY) {
+            const float g = __fmaf_rn(0.299f, v[0], __fmaf_rn(0.587f, v[1], __fmul_rn(0.114f, v[2])));
+            reinterpret_cast<float *>(o.p0)[c] = __fmaf_rn(g, J.scale[0], J.bias[0]);
+        } else if (CIN == 3 && o.p1) {
+            reinterpret_cast<float *>(o.p0)[c] = __fmaf_rn(v[0], J.scale[0], J.bias[0]);
+            reinterpret_cast<float *>(o.p1)[c] = __fmaf_rn(v[1], J.scale[1], J.bias[1]);
+            reinterpret_cast<float *>(o.p2)[c] = __fmaf_rn(v[2], J.scale[2], J.bias[2]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < CIN; ++k)
+                reinterpret_cast<float *>(o.p0)[c * CIN + k] = __fmaf_rn(v[k], J.scale[k], J.bias[k]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // The tile engine.
 // ---------------------------------------------------------------------------
@@ -239,17 +320,17 @@ template <int OP, int CIN, int OUTK, int TW, int TH>
 __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_y, uint8_t *smem,
                                              TileShared<TW, TH> &ts)
 {
-    TileInfo &ti = ts.ti;
     static_assert(TW % 32 == 0 && TH % kWarps == 0, "tile shape");
     using OT = OutTraits<OUTK, CIN>;
     constexpr int dC = OT::dC;
     constexpr int ES = OT::esize;
-    constexpr int NPL = (OT::is_f32 && dC == 3) ? 3 : 1;   // planes when CHW
+    constexpr int CPL = TW / 32;     // columns per lane
+    TileInfo &ti = ts.ti;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tx0 = tile_x * TW, ty0 = tile_y * TH;
     const int nx = min(TW, J.w - tx0), ny = min(TH, J.h - ty0);
 
-    // ---- 1. axis tables (resize) and source footprint ----------------------------
+    // ---- 1. plan -----------------------------------------------------------------
     if (OP == OP_RESIZE) {
         static_assert(TW + TH <= kThreads, "one axis entry per thread");
         if (tid < TW) {
@@ -265,218 +346,271 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             ts.ry0[r] = i0; ts.rqd[r] = q | ((i1 - i0) << 16); ts.rf[r] = f;
         }
         __syncthreads();
-    }
-    if (tid == 0) {
-        int fx0, fx1, fy0, fy1;
+        if (tid == 0) {
+            ti.fx0 = ts.cx0[0];
+            ti.fx1 = ts.cx0[nx - 1] + (ts.cqd[nx - 1] >> 16);
+            ti.fy0 = ts.ry0[0];
+            ti.fy1 = ts.ry0[ny - 1] + (ts.rqd[ny - 1] >> 16);
+        }
+    } else if (warp == 0) {
+        // Lanes 0..3 map one tile corner each; the box is their hull, one pixel wider
+        // on the low side and three on the high side (floor, second tap, the fast form's
+        // (x0 + 1, x0 + 2) pair, fp32 rounding of interior pixels).
+        const int cx = (lane & 1) ? tx0 + nx - 1 : tx0, cy = (lane & 2) ? ty0 + ny - 1 : ty0;
+        float sx = 0.f, sy = 0.f;
         bool ok = true;
-        if (OP == OP_RESIZE) {
-            fx0 = ts.cx0[0];
-            fx1 = ts.cx0[nx - 1] + (ts.cqd[nx - 1] >> 16);
-            fy0 = ts.ry0[0];
-            fy1 = ts.ry0[ny - 1] + (ts.rqd[ny - 1] >> 16);
-        } else {
-            float mnx = 3.4e38f, mxx = -3.4e38f, mny = 3.4e38f, mxy = -3.4e38f;
-            const int cx[2] = {tx0, tx0 + nx - 1}, cy[2] = {ty0, ty0 + ny - 1};
-            for (int a = 0; a < 2; ++a)
-                for (int b = 0; b < 2; ++b) {
-                    float sx, sy;
-                    ok = ok && warp_coord(J.M, cx[a], cy[b], sx, sy) && fabsf(sx) < 1048576.f &&
-                         fabsf(sy) < 1048576.f;
-                    mnx = fminf(mnx, sx); mxx = fmaxf(mxx, sx);
-                    mny = fminf(mny, sy); mxy = fmaxf(mxy, sy);
-                }
-            if (ok) {
-                fx0 = max((int)floorf(mnx) - 1, 0);
-                fx1 = min((int)floorf(mxx) + 2, J.W - 1);
-                fy0 = max((int)floorf(mny) - 1, 0);
-                fy1 = min((int)floorf(mxy) + 2, J.H - 1);
-                ok = fx0 <= fx1 && fy0 <= fy1;
+        if (lane < 4) ok = warp_coord(J.M, cx, cy, sx, sy) && fabsf(sx) < 1048576.f && fabsf(sy) < 1048576.f;
+        float mnx = lane < 4 ? sx : 3.0e38f, mxx = lane < 4 ? sx : -3.0e38f;
+        float mny = lane < 4 ? sy : 3.0e38f, mxy = lane < 4 ? sy : -3.0e38f;
+#pragma unroll
+        for (int o = 1; o < 4; o <<= 1) {
+            mnx = fminf(mnx, __shfl_xor_sync(0xffffffffu, mnx, o));
+            mxx = fmaxf(mxx, __shfl_xor_sync(0xffffffffu, mxx, o));
+            mny = fminf(mny, __shfl_xor_sync(0xffffffffu, mny, o));
+            mxy = fmaxf(mxy, __shfl_xor_sync(0xffffffffu, mxy, o));
+        }
+        const bool all_ok = __all_sync(0xffffffffu, ok);
+        if (lane == 0) {
+            int fx0 = 0, fx1 = -1, fy0 = 0, fy1 = -1, fast = 0;
+            if (all_ok) {
+                const int ax0 = (int)floorf(mnx) - 1, ax1 = (int)floorf(mxx) + 3;
+                const int ay0 = (int)floorf(mny) - 1, ay1 = (int)floorf(mxy) + 3;
+                fx0 = max(ax0, 0); fx1 = min(ax1, J.W - 1);
+                fy0 = max(ay0, 0); fy1 = min(ay1, J.H - 1);
+                fast = J.allow_fast && fx0 == ax0 && fx1 == ax1 && fy0 == ay0 && fy1 == ay1 &&
+                       mxx < 4093.f && mxy < 4093.f;
             }
+            ti.fx0 = fx0; ti.fx1 = fx1; ti.fy0 = fy0; ti.fy1 = fy1;
+            ti.fast = fast;
         }
-        int srow = 0;
-        if (ok) {
-            srow = round16((fx1 - fx0 + 1) * CIN + 15);
-            const long long need = (long long)(fy1 - fy0 + 1) * srow + 16;
-            ok = need <= J.foot_budget;
-        }
-        ti.fx0 = ok ? fx0 : 0; ti.fx1 = ok ? fx1 : -1;
-        ti.fy0 = ok ? fy0 : 0; ti.fy1 = ok ? fy1 : -1;
-        ti.srow = srow;
-        ti.staged = ok ? 1 : 0;
     }
     __syncthreads();
-    const int fx0 = ti.fx0, fx1 = ti.fx1, fy0 = ti.fy0, fy1 = ti.fy1, srow = ti.srow;
-    const bool staged = ti.staged != 0;
-    uint8_t *foot = smem;
-    uint8_t *ostage = smem + J.foot_budget;
+    if (tid == 0) {
+        const int cols = ti.fx1 - ti.fx0 + 1, rows = ti.fy1 - ti.fy0 + 1;
+        bool staged = cols >= 1 && rows >= 1 && J.foot_budget > 0;
+        const int srow = raw_row_bytes(max(cols, 1), CIN), sw = word_row(max(cols, 1));
+        if (staged) {
+            if (CIN == 3)
+                staged = (long long)rows * sw * 4 <= J.foot_budget && (long long)rows * srow <= J.region_b;
+            else
+                staged = (long long)rows * srow + 16 <= J.foot_budget;
+        }
+        ti.srow = srow;
+        ti.sw = sw;
+        ti.staged = staged;
+        ti.fast = (OP == OP_RESIZE ? 1 : ti.fast) && staged;   // resize taps always lie in the box
+    }
+    __syncthreads();
+    const int fx0 = ti.fx0, fx1 = ti.fx1, fy0 = ti.fy0, fy1 = ti.fy1;
+    const int srow = ti.srow, sw = ti.sw;
+    const bool staged = ti.staged != 0, fast = ti.fast != 0;
+    uint8_t *regA = smem;
+    uint8_t *regB = smem + J.foot_budget;
+    uint8_t *raw = CIN == 3 ? regB : regA;
+    uint8_t *ostage = regB;
+    const uint32_t *words = reinterpret_cast<const uint32_t *>(regA);
+    const int rows = fy1 - fy0 + 1, cols = fx1 - fx0 + 1;
 
+    // ---- 2. stage ----------------------------------------------------------------
     if (staged) {
-        const int L = (fx1 - fx0 + 1) * CIN;
-        for (int r = warp; r <= fy1 - fy0; r += kWarps) {
-            const uint8_t *a = J.src + (int64_t)(fy0 + r) * J.spitch + (int64_t)fx0 * CIN;
-            const uint8_t *G = reinterpret_cast<const uint8_t *>((uintptr_t)a & ~(uintptr_t)15);
-            const int phase = (int)((uintptr_t)a & 15);
-            const int nch = (phase + L + 15) >> 4;
-            uint8_t *srowp = foot + r * srow;
+        // Row r of the box is [a, a + L). It is staged as whole 16-byte chunks
+        // [align16(a), align16up(a + L)), clipped to the image's own byte range
+        // [ibeg, iend) so that every read stays inside the described buffer; bytes
+        // between rows (pitch padding) may be read but are never used. Only a chunk
+        // cut by ibeg or iend (the image's first or last 16 bytes) goes byte by byte.
+        const int L = cols * CIN;
+        const uintptr_t ibeg = (uintptr_t)J.src;
+        const uintptr_t iend = (uintptr_t)(J.src + (int64_t)(J.H - 1) * J.spitch + (int64_t)J.W * CIN);
+        for (int r = warp; r < rows; r += kWarps) {
+            const uintptr_t a = (uintptr_t)(J.src + (int64_t)(fy0 + r) * J.spitch + (int64_t)fx0 * CIN);
+            const uintptr_t G = a & ~(uintptr_t)15;
+            const uintptr_t lo = G > ibeg ? G : ibeg;
+            const uintptr_t e16 = (a + L + 15) & ~(uintptr_t)15;
+            const uintptr_t hi = e16 < iend ? e16 : iend;
+            const int nch = (int)((e16 - G) >> 4);
+            uint8_t *srowp = raw + r * srow;
             for (int j = lane; j < nch; j += 32) {
-                const int b0 = j * 16, b1 = b0 + 16;   // chunk bytes relative to G
-                if (b0 >= phase && b1 <= phase + L) {
-                    cp_async16(srowp + b0, G + b0);
+                const uintptr_t c0 = G + 16 * (uintptr_t)j;
+                if (c0 >= lo && c0 + 16 <= hi) {
+                    cp_async16(srowp + 16 * j, reinterpret_cast<const void *>(c0));
                 } else {
-                    const int lo = max(b0, phase), hi = min(b1, phase + L);
-                    for (int b = lo; b < hi; ++b) srowp[b] = __ldg(G + b);
+                    const uintptr_t b0 = c0 > lo ? c0 : lo, b1 = (c0 + 16 < hi) ? c0 + 16 : hi;
+                    for (uintptr_t b = b0; b < b1; ++b) srowp[b - G] = __ldg(reinterpret_cast<const uint8_t *>(b));
                 }
             }
         }
         cp_async_wait_all();
+        __syncthreads();
+        if (CIN == 3) {
+            // Re-lay each row as one word per pixel, 4 pixels (12 bytes) per step.
+            const int gpr = (cols + 3) >> 2;
+            const uint32_t rowphase0 = (uint32_t)(uintptr_t)(J.src + (int64_t)fx0 * 3);
+            for (int i = tid; i < rows * gpr; i += kThreads) {
+                const int r = i / gpr, g = i - r * gpr;
+                const int ph = (int)((rowphase0 + (uint32_t)((int64_t)(fy0 + r) * J.spitch)) & 15u);
+                const int o = ph + 12 * g;
+                const uint32_t *wp = reinterpret_cast<const uint32_t *>(raw + r * srow + (o & ~3));
+                const uint32_t sh = (uint32_t)(o & 3) * 8u;
+                const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2], w3 = wp[3];
+                const uint32_t b0 = __funnelshift_r(w0, w1, sh);
+                const uint32_t b1 = __funnelshift_r(w1, w2, sh);
+                const uint32_t b2 = __funnelshift_r(w2, w3, sh);
+                uint4 px;
+                px.x = b0;                              // R0 G0 B0 (R1)
+                px.y = __byte_perm(b0, b1, 0x6543);     // R1 G1 B1 (B1)
+                px.z = __byte_perm(b1, b2, 0x0432);     // R2 G2 B2
+                px.w = b2 >> 8;                         // R3 G3 B3
+                *reinterpret_cast<uint4 *>(regA + (r * sw + 4 * g) * 4) = px;
+            }
+            __syncthreads();
+        }
     }
-    __syncthreads();
 
-    // ---- 2. per-pixel compute into the output staging ---------------------------
-    // Output staging geometry: HWC -> one plane of rows of TW*dC*ES bytes;
-    // CHW (f32, 3 channels) -> three planes of rows of TW*4 bytes.
+    // ---- 3. compute --------------------------------------------------------------
     const bool chw = OT::is_f32 && dC == 3 && J.chw;
     const int orow = chw ? round16(TW * 4 + 15) : round16(TW * dC * ES + 15);
-    auto ophase = [&](int plane, int r) -> int {
-        const uint8_t *g = J.dst + (int64_t)(ty0 + r) * J.dpitch +
-                           (chw ? (int64_t)plane * J.dplane + (int64_t)tx0 * 4
-                                : (int64_t)tx0 * dC * ES);
-        return (int)((uintptr_t)g & 15);
+    // low address bits of output row 0 of the tile (plane 0): staging rows keep their phase
+    const uint32_t obase = (uint32_t)(uintptr_t)(J.dst + (int64_t)ty0 * J.dpitch +
+                                                 (chw ? (int64_t)tx0 * 4 : (int64_t)tx0 * dC * ES));
+    const uint32_t opitch = (uint32_t)J.dpitch, oplane = (uint32_t)J.dplane;
+    auto orow_of = [&](int r) -> ORow {
+        ORow o;
+        const uint32_t a = obase + (uint32_t)r * opitch;
+        o.p0 = ostage + r * orow + (a & 15u);
+        if (chw) {
+            o.p1 = ostage + (TH + r) * orow + ((a + oplane) & 15u);
+            o.p2 = ostage + (2 * TH + r) * orow + ((a + 2u * oplane) & 15u);
+        } else {
+            o.p1 = o.p2 = nullptr;
+        }
+        return o;
     };
 
-    // Per-lane column parameters (resize), read once from the tile tables.
-    constexpr int CPL = TW / 32;
-    int cx0[CPL], cdx[CPL], cq[CPL];
-    float cf[CPL];
-    if (OP == OP_RESIZE) {
-#pragma unroll
-        for (int j = 0; j < CPL; ++j) {
-            const int c = lane + 32 * j;
-            cx0[j] = ts.cx0[c]; cq[j] = ts.cqd[c] & 0xFFFF; cdx[j] = ts.cqd[c] >> 16; cf[j] = ts.cf[c];
-        }
-    }
-
-    const uint32_t sbase = (uint32_t)(uintptr_t)(J.src + (int64_t)fx0 * CIN);
-
-    for (int r = warp; r < ny; r += kWarps) {
-        const int y = ty0 + r;
-        int ry0 = 0, rdy = 0, rq = 0;
-        float rf = 0.f;
+    if (fast && CIN == 3) {
+        const int wbase = -(fy0 * sw + fx0);
         if (OP == OP_RESIZE) {
-            ry0 = ts.ry0[r]; rq = ts.rqd[r] & 0xFFFF; rdy = ts.rqd[r] >> 16; rf = ts.rf[r];
-        }
-        const int oph = ophase(0, r);
-        uint8_t *orowp = ostage + r * orow;
+            int xo[CPL], xo1[CPL], qxs[CPL];   // word offsets of the two column taps in a box row
+            float fxs[CPL];
 #pragma unroll
-        for (int j = 0; j < CPL; ++j) {
-            const int c = lane + 32 * j;
-            if (c >= nx) continue;
-            const int x = tx0 + c;
-            int x0, y0, qx, qy, dx, dy;
-            float fx, fy;
-            bool valid = true;   // false: sample outside the coordinate range -> 0
-            if (OP == OP_RESIZE) {
-                x0 = cx0[j]; dx = cdx[j]; qx = cq[j]; fx = cf[j];
-                y0 = ry0; dy = rdy; qy = rq; fy = rf;
-            } else {
-                float sx, sy;
-                valid = warp_coord(J.M, x, y, sx, sy);
-                x0 = y0 = qx = qy = 0; fx = fy = 0.f;
-                if (valid) {
-                    warp_weight(sx, x0, qx);
-                    warp_weight(sy, y0, qy);
-                    if (OT::is_f32) {
+            for (int j = 0; j < CPL; ++j) {
+                const int c = lane + 32 * j;
+                xo[j] = ts.cx0[c] - fx0;
+                xo1[j] = xo[j] + (ts.cqd[c] >> 16);
+                qxs[j] = ts.cqd[c] & 0xFFFF;
+                fxs[j] = ts.cf[c];
+            }
+            for (int r = warp; r < ny; r += kWarps) {
+                const int y0 = ts.ry0[r], qy = ts.rqd[r] & 0xFFFF, dy = ts.rqd[r] >> 16;
+                const float fy = ts.rf[r];
+                const uint32_t *w0 = words + (y0 - fy0) * sw;
+                const uint32_t *w1 = w0 + dy * sw;
+                const ORow o = orow_of(r);
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) {
+                    const int c = lane + 32 * j;
+                    if (c < nx)
+                        emit<CIN, OUTK>(J, o, c, w0[xo[j]], w0[xo1[j]], w1[xo[j]], w1[xo1[j]], qxs[j], qy,
+                                        fxs[j], fy);
+                }
+            }
+        } else {
+            // warp: per pixel a = m00 (x + 1/2) + row term (fp32 fma), then the fast weight form
+            float xcs[CPL];
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) xcs[j] = __fadd_rn((float)(tx0 + lane + 32 * j), 0.5f);
+            for (int r = warp; r < ny; r += kWarps) {
+                const float yc = __fadd_rn((float)(ty0 + r), 0.5f);
+                const float rx = __fmaf_rn(J.M[1], yc, J.M[2]);
+                const float ry = __fmaf_rn(J.M[4], yc, J.M[5]);
+                const ORow o = orow_of(r);
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) {
+                    const int c = lane + 32 * j;
+                    if (c < nx) {
+                        const float ax = __fmaf_rn(J.M[0], xcs[j], rx);
+                        const float ay = __fmaf_rn(J.M[3], xcs[j], ry);
+                        int x0, y0, qx = 0, qy = 0;
+                        float fx = 0.f, fy = 0.f;
+                        if (!OT::is_f32) {
+                            const int Tx = warp_fixed_fast(ax), Ty = warp_fixed_fast(ay);
+                            x0 = Tx >> 11; qx = Tx & 2047;
+                            y0 = Ty >> 11; qy = Ty & 2047;
+                        } else {
+                            const float sx = __fsub_rn(ax, 0.5f), sy = __fsub_rn(ay, 0.5f);
+                            x0 = __float2int_rd(sx);
+                            y0 = __float2int_rd(sy);
+                            // exact float of x0 in [0, 2^23): 2^23 + x0 has x0 in its mantissa
+                            fx = __fsub_rn(sx, __fsub_rn(__int_as_float(0x4B000000 + x0), 8388608.f));
+                            fy = __fsub_rn(sy, __fsub_rn(__int_as_float(0x4B000000 + y0), 8388608.f));
+                        }
+                        const uint32_t *w0 = words + (y0 * sw + x0 + wbase);
+                        emit<CIN, OUTK>(J, o, c, w0[0], w0[1], w0[sw], w0[sw + 1], qx, qy, fx, fy);
+                    }
+                }
+            }
+        }
+    } else {
+        // General path: per-pixel coordinates with the full rules; taps from the
+        // staged box when inside it, else from global memory (zero outside the image).
+        const uint32_t rowphase0 = (uint32_t)(uintptr_t)(J.src + (int64_t)fx0 * CIN);
+        for (int r = warp; r < ny; r += kWarps) {
+            const int y = ty0 + r;
+            const ORow o = orow_of(r);
+            for (int j = 0; j < CPL; ++j) {
+                const int c = lane + 32 * j;
+                if (c >= nx) continue;
+                const int x = tx0 + c;
+                int x0 = 0, y0 = 0, qx = 0, qy = 0, dx = 1, dy = 1;
+                float fx = 0.f, fy = 0.f;
+                bool valid = true;
+                if (OP == OP_RESIZE) {
+                    x0 = ts.cx0[c]; dx = ts.cqd[c] >> 16; qx = ts.cqd[c] & 0xFFFF; fx = ts.cf[c];
+                    y0 = ts.ry0[r]; dy = ts.rqd[r] >> 16; qy = ts.rqd[r] & 0xFFFF; fy = ts.rf[r];
+                } else {
+                    float sx, sy;
+                    valid = warp_coord(J.M, x, y, sx, sy);
+                    if (valid) {
+                        warp_weight(sx, x0, qx);
+                        warp_weight(sy, y0, qy);
                         fx = __fsub_rn(sx, floorf(sx));
                         fy = __fsub_rn(sy, floorf(sy));
                     }
                 }
-                dx = 1; dy = 1;
-            }
-            // ---- fetch taps as byte pairs of each source row:
-            //   CIN 3: lo = R0 G0 B0 R1, hi = G1 B1 (taps x0 and x0 + 1);
-            //   CIN 1: lo = p0 | p1 << 8.
-            // Resize at the right/bottom edge has dx or dy = 0 and a zero weight on
-            // the second tap, so reading x0 + 1 (or row y0) there changes nothing.
-            uint32_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
-            if (valid) {
-                const bool in_box = staged && x0 >= fx0 && x0 + dx <= fx1 && y0 >= fy0 && y0 + dy <= fy1;
-                if (in_box) {
-                    const int r0 = y0 - fy0, r1 = r0 + dy;
-                    const int ph0 = (int)((sbase + (uint32_t)((int64_t)y0 * J.spitch)) & 15u);
-                    const int ph1 = (int)((sbase + (uint32_t)((int64_t)(y0 + dy) * J.spitch)) & 15u);
-                    const int xo = (x0 - fx0) * CIN;
-                    if (CIN == 3) {
-                        lds6(foot + r0 * srow, ph0 + xo, lo0, hi0);
-                        lds6(foot + r1 * srow, ph1 + xo, lo1, hi1);
+                uint32_t p00 = 0, p01 = 0, p10 = 0, p11 = 0;
+                if (valid) {
+                    const bool in_box = staged && x0 >= fx0 && x0 + dx <= fx1 && y0 >= fy0 && y0 + dy <= fy1;
+                    if (in_box && CIN == 3) {
+                        const uint32_t *w0 = words + ((y0 - fy0) * sw + (x0 - fx0));
+                        const uint32_t *w1 = w0 + dy * sw;
+                        p00 = w0[0]; p01 = w0[dx]; p10 = w1[0]; p11 = w1[dx];
+                    } else if (in_box) {
+                        const int r0 = y0 - fy0, r1 = r0 + dy;
+                        const int ph0 = (int)((rowphase0 + (uint32_t)((int64_t)y0 * J.spitch)) & 15u);
+                        const int ph1 = (int)((rowphase0 + (uint32_t)((int64_t)(y0 + dy) * J.spitch)) & 15u);
+                        const uint8_t *s0 = raw + r0 * srow + ph0 + (x0 - fx0);
+                        const uint8_t *s1 = raw + r1 * srow + ph1 + (x0 - fx0);
+                        p00 = s0[0]; p01 = s0[dx]; p10 = s1[0]; p11 = s1[dx];
+                    } else if (CIN == 3) {
+                        p00 = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0);
+                        p01 = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0 + dx);
+                        p10 = ldg_px3(J.src, J.spitch, J.H, J.W, y0 + dy, x0);
+                        p11 = ldg_px3(J.src, J.spitch, J.H, J.W, y0 + dy, x0 + dx);
                     } else {
-                        const uint8_t *s0 = foot + r0 * srow + ph0 + xo;
-                        const uint8_t *s1 = foot + r1 * srow + ph1 + xo;
-                        lo0 = (uint32_t)s0[0] | ((uint32_t)s0[1] << 8);
-                        lo1 = (uint32_t)s1[0] | ((uint32_t)s1[1] << 8);
+                        p00 = ldg_px1(J.src, J.spitch, J.H, J.W, y0, x0);
+                        p01 = ldg_px1(J.src, J.spitch, J.H, J.W, y0, x0 + dx);
+                        p10 = ldg_px1(J.src, J.spitch, J.H, J.W, y0 + dy, x0);
+                        p11 = ldg_px1(J.src, J.spitch, J.H, J.W, y0 + dy, x0 + dx);
                     }
-                } else if (CIN == 3) {
-                    const uint32_t a = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0);
-                    const uint32_t b = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0 + dx);
-                    const uint32_t c2 = ldg_px3(J.src, J.spitch, J.H, J.W, y0 + dy, x0);
-                    const uint32_t d = ldg_px3(J.src, J.spitch, J.H, J.W, y0 + dy, x0 + dx);
-                    lo0 = a | (b << 24); hi0 = b >> 8;
-                    lo1 = c2 | (d << 24); hi1 = d >> 8;
-                } else {
-                    lo0 = ldg_px1(J.src, J.spitch, J.H, J.W, y0, x0) |
-                          (ldg_px1(J.src, J.spitch, J.H, J.W, y0, x0 + dx) << 8);
-                    lo1 = ldg_px1(J.src, J.spitch, J.H, J.W, y0 + dy, x0) |
-                          (ldg_px1(J.src, J.spitch, J.H, J.W, y0 + dy, x0 + dx) << 8);
                 }
-            }
-            // ---- blend and stage
-            if (!OT::is_f32) {
-                const uint32_t wx = (uint32_t)(2048 - qx) | ((uint32_t)qx << 16);
-                uint32_t o0, o1 = 0, o2 = 0;
-                if (CIN == 3) {
-                    const U8x3 a = hblend3(lo0, hi0, wx), b = hblend3(lo1, hi1, wx);
-                    o0 = vblend(a.r, b.r, qy); o1 = vblend(a.g, b.g, qy); o2 = vblend(a.b, b.b, qy);
-                } else {
-                    o0 = vblend(__dp2a_lo(wx, lo0, 0u), __dp2a_lo(wx, lo1, 0u), qy);
-                }
-                uint8_t *op = orowp + oph + c * dC;
-                if (OUTK == OUT_U8_GRAY) {
-                    op[0] = (uint8_t)gray_u8(o0, o1, o2);
-                } else {
-                    op[0] = (uint8_t)o0;
-                    if (CIN == 3) { op[1] = (uint8_t)o1; op[2] = (uint8_t)o2; }
-                }
-            } else {
-                float v[3];
-#pragma unroll
-                for (int k = 0; k < CIN; ++k) {
-                    const float a = pair_f(lo0, hi0, k), b = pair_f(lo0, hi0, CIN + k);
-                    const float d0 = pair_f(lo1, hi1, k), d1 = pair_f(lo1, hi1, CIN + k);
-                    const float h0 = __fmaf_rn(fx, __fsub_rn(b, a), a);
-                    const float h1 = __fmaf_rn(fx, __fsub_rn(d1, d0), d0);
-                    v[k] = __fmaf_rn(fy, __fsub_rn(h1, h0), h0);
-                }
-                if (OUTK == OUT_F32_GRAY) {
-                    const float g = __fmaf_rn(0.299f, v[0], __fmaf_rn(0.587f, v[1], __fmul_rn(0.114f, v[2])));
-                    *reinterpret_cast<float *>(orowp + oph + c * 4) = __fmaf_rn(g, J.scale[0], J.bias[0]);
-                } else if (chw) {
-#pragma unroll
-                    for (int k = 0; k < CIN; ++k) {
-                        uint8_t *pl = ostage + k * TH * orow + r * orow + ophase(k, r);
-                        *reinterpret_cast<float *>(pl + c * 4) = __fmaf_rn(v[k], J.scale[k], J.bias[k]);
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < CIN; ++k)
-                        *reinterpret_cast<float *>(orowp + oph + (c * CIN + k) * 4) =
-                            __fmaf_rn(v[k], J.scale[k], J.bias[k]);
-                }
+                emit<CIN, OUTK>(J, o, c, p00, p01, p10, p11, qx, qy, fx, fy);
             }
         }
     }
     __syncthreads();
 
-    // ---- 3. write-out: one warp per (plane, row), 16-byte chunks --------------------
-    const int nplanes = chw ? NPL : 1;
+    // ---- 4. write-out: one warp per (plane, row); 16-byte chunks for the aligned
+    // body, one byte per lane for the (at most 15 + 15) head and tail bytes.
+    const int nplanes = chw ? 3 : 1;
     const int seglen = chw ? nx * 4 : nx * dC * ES;
     for (int s = warp; s < nplanes * ny; s += kWarps) {
         const int pl = s / ny, r = s - pl * ny;
@@ -485,15 +619,17 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         const int phase = (int)((uintptr_t)g & 15);
         uint8_t *G = g - phase;
         const uint8_t *S = ostage + (pl * TH + r) * orow;
-        const int nch = (phase + seglen + 15) >> 4;
-        for (int j = lane; j < nch; j += 32) {
-            const int b0 = j * 16, b1 = b0 + 16;
-            if (b0 >= phase && b1 <= phase + seglen) {
-                *reinterpret_cast<uint4 *>(G + b0) = *reinterpret_cast<const uint4 *>(S + b0);
-            } else {
-                const int lo = max(b0, phase), hi = min(b1, phase + seglen);
-                for (int b = lo; b < hi; ++b) G[b] = S[b];
-            }
+        const int end = phase + seglen;
+        const int jf = (phase + 15) >> 4, jl = end >> 4;   // full chunks: [jf, jl)
+        for (int j = jf + lane; j < jl; j += 32)
+            *reinterpret_cast<uint4 *>(G + 16 * j) = *reinterpret_cast<const uint4 *>(S + 16 * j);
+        const int head_end = min(jf * 16, end);
+        if (lane < 16) {
+            const int b = phase + lane;
+            if (b < head_end) G[b] = S[b];
+        } else if (jl >= jf) {
+            const int b = jl * 16 + (lane - 16);
+            if (b < end) G[b] = S[b];
         }
     }
     __syncthreads();

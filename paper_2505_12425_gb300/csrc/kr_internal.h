@@ -13,8 +13,11 @@ namespace kr {
 
 // Largest number of per-image warp matrices carried by one launch's parameters.
 constexpr int kMaxMPerLaunch = 128;
-// Shared-memory cap for one tile's source footprint.
+// Shared-memory caps: region A (the staged box: one word per pixel for 3-channel
+// sources, raw bytes for 1-channel sources) and region B (raw rows of a 3-channel
+// box, later the output tile).
 constexpr int kFootCap = 40 * 1024;
+constexpr int kRegionBCap = 34 * 1024;
 
 // A validated single-image-op request, pointers as device addresses.
 struct OpDesc {
@@ -46,9 +49,18 @@ struct GrayDesc {
 };
 cudaError_t launch_gray(const GrayDesc &d, cudaStream_t stream);
 
-// Shared-memory footprint budget of one tile (bytes, multiple of 16; 0 = no staging).
-int foot_budget_resize(int cin, int H, int W, int h, int w, int tw, int th);
-int foot_budget_warp(int cin, int H, int W, const float *M, int tw, int th);
+// Shared-memory budget of one tile: region A bytes (0 = no staging) and region B bytes
+// (at least out_bytes, the output tile). Multiples of 16.
+struct Budget {
+    int a;
+    int b;
+};
+Budget budget_resize(int cin, int H, int W, int h, int w, int tw, int th, int out_bytes);
+Budget budget_warp(int cin, int H, int W, const float *M, int tw, int th, int out_bytes);
+// Warp maps whose terms |m00| w, |m01| h, |m02| (and the second row) stay below 2^19 keep
+// every intermediate of the fp32 coordinate below 2^20, so interior pixels deviate from the
+// corner hull by far less than the box margin: such maps may use the fast tile path.
+bool warp_allows_fast(const float *M, int h, int w);
 
 // Validation + descriptor construction (kr_abi.cu); nothing is enqueued.
 kr_status build_resample(int op, const kr_image_t *src, const kr_image_t *dst, const kr_post_t *post,

@@ -23,6 +23,8 @@ struct OpParams {
     int32_t h, w;
     int32_t chw;
     int32_t foot_budget;
+    int32_t region_b;
+    uint32_t fast_mask[(kMaxMPerLaunch + 31) / 32];   // warp: images whose map allows the fast path
     float scale[3], bias[3];
     float M[kMaxMPerLaunch][6];
 };
@@ -45,6 +47,8 @@ __global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constan
     J.w = p.w;
     J.chw = p.chw;
     J.foot_budget = p.foot_budget;
+    J.region_b = p.region_b;
+    J.allow_fast = OP == OP_WARP ? (int)((p.fast_mask[z >> 5] >> (z & 31)) & 1u) : 1;
 #pragma unroll
     for (int k = 0; k < 6; ++k) J.M[k] = OP == OP_WARP ? p.M[z][k] : 0.f;
 #pragma unroll
@@ -56,28 +60,61 @@ __global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constan
 }
 
 // ---------------------------------------------------------------------------
-// Footprint budgets
+// Shared-memory budgets
 // ---------------------------------------------------------------------------
-int foot_budget_resize(int cin, int H, int W, int h, int w, int tw, int th)
+static Budget budget_for(int cin, double cols_d, double rows_d, int H, int W, int out_bytes, bool clamp)
+{
+    const int cols = (int)std::min<double>(cols_d, W), rows = (int)std::min<double>(rows_d, H);
+    long long a, raw;
+    if (cin == 3) {
+        a = (long long)rows * word_row(cols) * 4;
+        raw = (long long)rows * raw_row_bytes(cols, 3);
+    } else {
+        a = (long long)rows * raw_row_bytes(cols, 1) + 16;
+        raw = 0;
+    }
+    Budget b;
+    if (a <= kFootCap && raw <= kRegionBCap) {
+        b.a = round16((int)a);
+        b.b = round16((int)std::max<long long>(out_bytes, raw));
+    } else if (clamp) {
+        // tiles whose box fits these caps are staged, the others take the general path
+        b.a = kFootCap;
+        b.b = round16(std::max(out_bytes, cin == 3 ? kRegionBCap : 0));
+    } else {
+        b.a = 0;
+        b.b = round16(out_bytes);
+    }
+    return b;
+}
+
+Budget budget_resize(int cin, int H, int W, int h, int w, int tw, int th, int out_bytes)
 {
     // Taps of tw consecutive columns span at most (tw - 1) W / w + 2 source columns.
     const double cols = std::ceil((tw - 1) * (double)W / w) + 3;
     const double rows = std::ceil((th - 1) * (double)H / h) + 3;
-    const double c = std::min<double>(cols, W), r = std::min<double>(rows, H);
-    const double need = r * round16((int)c * cin + 15) + 16;
-    return need <= kFootCap ? round16((int)need) : 0;
+    return budget_for(cin, cols, rows, H, W, out_bytes, false);
 }
 
-int foot_budget_warp(int cin, int H, int W, const float *M, int tw, int th)
+Budget budget_warp(int cin, int H, int W, const float *M, int tw, int th, int out_bytes)
 {
-    // The staged box of a tile spans at most |m00|(tw-1) + |m01|(th-1) columns plus
-    // five (floor, the second tap, one pixel of rounding margin on each side).
+    // The box of a tile spans at most |m00|(tw-1) + |m01|(th-1) columns plus six
+    // (floor, one pixel low margin, three high margin, rounding).
     const double cols = std::ceil(std::fabs(M[0]) * (tw - 1) + std::fabs(M[1]) * (th - 1)) + 6;
     const double rows = std::ceil(std::fabs(M[3]) * (tw - 1) + std::fabs(M[4]) * (th - 1)) + 6;
-    if (!(cols < 1e7 && rows < 1e7)) return kFootCap;
-    const double c = std::min<double>(cols, W), r = std::min<double>(rows, H);
-    const double need = r * round16((int)c * cin + 15) + 16;
-    return round16((int)std::min<double>(need, kFootCap));
+    if (!(cols < 1e7 && rows < 1e7)) return budget_for(cin, 1e7, 1e7, H, W, out_bytes, true);
+    return budget_for(cin, cols, rows, H, W, out_bytes, true);
+}
+
+bool warp_allows_fast(const float *M, int h, int w)
+{
+    const double lim = 524288.0;   // 2^19
+    for (int r = 0; r < 2; ++r) {
+        const float *m = M + 3 * r;
+        if (!(std::fabs(m[0]) * (w + 1) < lim && std::fabs(m[1]) * (h + 1) < lim && std::fabs(m[2]) < lim))
+            return false;
+    }
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -93,7 +130,7 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
     cudaGetDevice(&dev);
     if (dev >= 32 || !(attr_done & (1u << dev))) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kFootCap + out_stage_bytes<OUTK, CIN, TW, TH>());
+                                             kFootCap + std::max(kRegionBCap, out_stage_bytes<OUTK, CIN, TW, TH>()));
         if (e != cudaSuccess) return e;
         if (dev < 32) __atomic_fetch_or(&attr_done, 1u << dev, __ATOMIC_RELAXED);
     }
@@ -119,19 +156,27 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
     const int per_launch = OP == OP_WARP ? kMaxMPerLaunch : 65535;
     for (int b0 = 0; b0 < d.batch; b0 += per_launch) {
         const int nb = std::min(per_launch, d.batch - b0);
-        int budget = 0;
+        constexpr int ob = out_stage_bytes<OUTK, CIN, TW, TH>();
+        Budget bud;
+        std::memset(p.fast_mask, 0, sizeof(p.fast_mask));
         if (OP == OP_RESIZE) {
-            budget = foot_budget_resize(CIN, d.H, d.W, d.h, d.w, TW, TH);
+            bud = budget_resize(CIN, d.H, d.W, d.h, d.w, TW, TH, ob);
         } else {
+            bud.a = 0;
+            bud.b = round16(ob);
             for (int i = 0; i < nb; ++i) {
                 for (int k = 0; k < 6; ++k) p.M[i][k] = d.M[(size_t)(b0 + i) * 6 + k];
-                budget = std::max(budget, foot_budget_warp(CIN, d.H, d.W, p.M[i], TW, TH));
+                const Budget bi = budget_warp(CIN, d.H, d.W, p.M[i], TW, TH, ob);
+                bud.a = std::max(bud.a, bi.a);
+                bud.b = std::max(bud.b, bi.b);
+                if (warp_allows_fast(p.M[i], d.h, d.w)) p.fast_mask[i >> 5] |= 1u << (i & 31);
             }
         }
-        p.foot_budget = budget;
+        p.foot_budget = bud.a;
+        p.region_b = bud.b;
         p.src = d.src + (int64_t)b0 * d.sbatch;
         p.dst = d.dst + (int64_t)b0 * d.dbatch;
-        const size_t smem = (size_t)budget + out_stage_bytes<OUTK, CIN, TW, TH>();
+        const size_t smem = (size_t)bud.a + bud.b;
         dim3 grid(tiles_x, tiles_y, nb);
         kern<<<grid, kThreads, smem, stream>>>(p);
         cudaError_t e = cudaGetLastError();
