@@ -159,9 +159,9 @@ typedef struct {
 } kr_work_t;
 
 /*
- * Launch options. tile_config: -1 = the autotuned choice for this batch's
- * shape class (the first submit of a class tunes it, see kr_autotune_batch),
- * or an index < kr_tile_config_count(). ctas_per_sm: 0 = the occupancy limit.
+ * Launch options. tile_config: -1 = the choice kr_autotune_batch cached for
+ * this batch's shape class, else configuration 0; or an index
+ * < kr_tile_config_count(). ctas_per_sm: 0 = the occupancy limit.
  * use_graph: nonzero = replay the launch from a CUDA graph captured once per
  * (stream, workspace, configuration).
  */
@@ -185,6 +185,40 @@ size_t kr_batch_workspace_size(int32_t max_items);
  */
 kr_status kr_batch_submit(const kr_work_t *items, int32_t n, void *workspace,
                           size_t ws_bytes, const kr_batch_opts_t *opts, kr_stream_t stream);
+
+/*
+ * kr_batch_submit without a workspace and without any allocation.
+ *
+ * The paper has no counterpart of this call. It exists for callers that cannot
+ * allocate device memory at the point where they submit work: real-time loops
+ * that forbid allocation on their hot path (an allocation can block or fail at
+ * an unpredictable moment), host frameworks whose own allocator owns all device
+ * memory, and code that cannot keep a workspace alive between calls. Such a
+ * caller passes only the items (their images are the inputs and outputs it
+ * already owns); the work list goes into a fixed device array inside this
+ * library instead of a workspace.
+ *
+ * Limits and behaviour:
+ *   - at most KR_BATCH_NOALLOC_MAX_ITEMS items per call; more gives
+ *     KR_ERR_NO_SPACE with nothing enqueued;
+ *   - the array (about 132 KiB) is a file-scope __device__ array: every GPU that
+ *     loads the library holds it until the process exits;
+ *   - the first call on a device looks up the array's device address for that
+ *     device (cudaGetSymbolAddress); make that first call before any stream
+ *     capture;
+ *   - every call shares the one array and overwrites it (the tile counter is
+ *     reset by each call's copy): calls whose work may overlap on the GPU race,
+ *     so serialise them (one stream, or events between streams);
+ *   - calls no cudaMalloc, cudaFree, cudaHostAlloc or other allocating routine;
+ *     the work list is copied from a fixed host array with cudaMemcpyAsync, and
+ *     the call returns once that array has been read;
+ *   - opts: tile_config < 0 means configuration 0 (no autotune lookup),
+ *     ctas_per_sm as for kr_batch_submit, use_graph is ignored.
+ * Results equal kr_batch_submit's bit for bit.
+ */
+#define KR_BATCH_NOALLOC_MAX_ITEMS 1024
+kr_status kr_batch_submit_noalloc(const kr_work_t *items, int32_t n, const kr_batch_opts_t *opts,
+                                  kr_stream_t stream);
 
 /* Number of tile configurations the batch launch can use, and their shapes. */
 int32_t kr_tile_config_count(void);

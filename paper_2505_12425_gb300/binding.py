@@ -81,6 +81,7 @@ def load():
         lib.kr_batch_workspace_size.restype = ctypes.c_size_t
         lib.kr_batch_submit.argtypes = [P(KrWork), ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
                                         P(KrBatchOpts), ctypes.c_void_p]
+        lib.kr_batch_submit_noalloc.argtypes = [P(KrWork), ctypes.c_int32, P(KrBatchOpts), ctypes.c_void_p]
         lib.kr_tile_config_count.argtypes = []
         lib.kr_tile_config_count.restype = ctypes.c_int32
         lib.kr_tile_config_shape.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32)]
@@ -95,6 +96,7 @@ def load():
         lib.kr_shutdown.argtypes = []
         lib.kr_shutdown.restype = None
         for f in ("kr_resize_bilinear", "kr_warp_affine", "kr_rgb_to_gray", "kr_batch_submit",
+                  "kr_batch_submit_noalloc",
                   "kr_tile_config_shape", "kr_autotune_batch", "kr_autotune_save", "kr_autotune_load"):
             getattr(lib, f).restype = S
         _lib = lib
@@ -237,6 +239,19 @@ def kr_batch_submit(items, workspace: torch.Tensor, tile_config: int = -1, ctas_
     _check(lib.kr_batch_submit(arr, len(arr), ctypes.c_void_p(workspace.data_ptr()),
                                workspace.numel() * workspace.element_size(), ctypes.byref(o),
                                _stream(stream)), "kr_batch_submit")
+
+
+KR_BATCH_NOALLOC_MAX_ITEMS = 1024
+
+
+def kr_batch_submit_noalloc(items, tile_config: int = -1, ctas_per_sm: int = 0, stream=None):
+    """kr_batch_submit without a workspace: for callers that may not allocate device memory
+    when they submit (the work list goes into a fixed device array inside the library)."""
+    lib = load()
+    arr = items if isinstance(items, ctypes.Array) else work_array(items)
+    o = KrBatchOpts(tile_config, ctas_per_sm, 0)
+    _check(lib.kr_batch_submit_noalloc(arr, len(arr), ctypes.byref(o), _stream(stream)),
+           "kr_batch_submit_noalloc")
 
 
 def kr_tile_config_count() -> int:

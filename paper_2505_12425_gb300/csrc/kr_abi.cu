@@ -2,19 +2,20 @@
 // (everything is checked on the host before anything is enqueued), mapping of
 // the public descriptors to the internal launch descriptors, status text.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
-#include <string>
 
 #include "kr_device.cuh"
 #include "kr_internal.h"
 
 namespace kr {
 
-static thread_local std::string g_last_error;
+static thread_local char g_last_error[256];
 
-void set_last_error(const std::string &what, cudaError_t e)
+void set_last_error(const char *what, cudaError_t e)
 {
-    g_last_error = what + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%s)", what, cudaGetErrorName(e),
+                  cudaGetErrorString(e));
 }
 
 // Largest accepted image side.
@@ -217,6 +218,6 @@ const char *kr_status_string(kr_status s)
     return "unknown status";
 }
 
-const char *kr_last_error(void) { return g_last_error.c_str(); }
+const char *kr_last_error(void) { return g_last_error; }
 
 }  // extern "C"

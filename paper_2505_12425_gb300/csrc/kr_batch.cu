@@ -57,8 +57,11 @@ static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 constexpr int kind_of(int op, int cin, int outk) { return op | (cin << 4) | (outk << 8); }
 constexpr int KIND_GRAY = 0x1000;
 
-static size_t prefix_bytes(int n) { return ((size_t)(n + 1) * 4 + 15) & ~(size_t)15; }
-static size_t worklist_bytes(int n) { return sizeof(WsHeader) + (size_t)n * sizeof(WorkItem) + prefix_bytes(n); }
+static constexpr size_t prefix_bytes(int n) { return ((size_t)(n + 1) * 4 + 15) & ~(size_t)15; }
+static constexpr size_t worklist_bytes(int n)
+{
+    return sizeof(WsHeader) + (size_t)n * sizeof(WorkItem) + prefix_bytes(n);
+}
 
 // Gray tile: TW x TH pixels, no staging (3 bytes in, 1 byte out per pixel).
 template <int TW, int TH>
@@ -181,29 +184,24 @@ static int out_stage_of(int outk, int cin, int tw, int th)
 // ---------------------------------------------------------------------------
 // Host-side packing
 // ---------------------------------------------------------------------------
-struct Packed {
-    std::vector<WorkItem> items;
-    std::vector<int> prefix;
+struct PackInfo {
     int total_tiles = 0;
     size_t smem = 0;        // dynamic shared bytes the launch needs
     int opmask = 0;
     double out_px = 0;
 };
 
-// Validate all items and convert them into device work items for tile shape (tw, th).
-static kr_status pack_items(const kr_work_t *items, int n, int tw, int th, Packed &P)
+// Validate all items and write them as device work items for tile shape (tw, th) into
+// out[0..n) and their first-tile indices into prefix[0..n]. Allocates nothing.
+static kr_status pack_into(const kr_work_t *items, int n, int tw, int th, WorkItem *out, int *prefix,
+                           PackInfo &P)
 {
-    P.items.resize(n);
-    P.prefix.resize(n + 1);
-    P.total_tiles = 0;
-    P.smem = 0;
-    P.opmask = 0;
-    P.out_px = 0;
+    P = PackInfo();
     long long total = 0;
     for (int i = 0; i < n; ++i) {
         const kr_work_t &w = items[i];
         if (w.src.batch != 1 || w.dst.batch != 1) return KR_ERR_INVALID_ARG;
-        WorkItem &it = P.items[i];
+        WorkItem &it = out[i];
         std::memset(&it, 0, sizeof(it));
         if (w.op == KR_OP_GRAY) {
             GrayDesc g;
@@ -239,25 +237,45 @@ static kr_status pack_items(const kr_work_t *items, int n, int tw, int th, Packe
         P.out_px += (double)it.h * it.w;
         it.tiles_x = (it.w + tw - 1) / tw;
         const long long tiles = (long long)it.tiles_x * ((it.h + th - 1) / th);
-        P.prefix[i] = (int)total;
+        prefix[i] = (int)total;
         total += tiles;
         if (total > 0x7FFFFFFF) return KR_ERR_INVALID_ARG;
     }
-    P.prefix[n] = (int)total;
+    prefix[n] = (int)total;
     P.total_tiles = (int)total;
     return KR_OK;
 }
 
-static void write_worklist(const Packed &P, uint8_t *dst)
+// The work list of the submit path, in host memory.
+struct Packed {
+    std::vector<WorkItem> items;
+    std::vector<int> prefix;
+    PackInfo info;
+};
+
+static kr_status pack_items(const kr_work_t *items, int n, int tw, int th, Packed &P)
+{
+    P.items.resize(n);
+    P.prefix.resize(n + 1);
+    return pack_into(items, n, tw, th, P.items.data(), P.prefix.data(), P.info);
+}
+
+// Work-list image: header, items, tile prefix (the layout the kernel reads).
+static void write_worklist_raw(const WorkItem *items, const int *prefix, int n, int total_tiles, uint8_t *dst)
 {
     WsHeader h;
     std::memset(&h, 0, sizeof(h));
     h.next = 0;
-    h.n = (int)P.items.size();
-    h.total_tiles = P.total_tiles;
+    h.n = n;
+    h.total_tiles = total_tiles;
     std::memcpy(dst, &h, sizeof(h));
-    std::memcpy(dst + sizeof(h), P.items.data(), P.items.size() * sizeof(WorkItem));
-    std::memcpy(dst + sizeof(h) + P.items.size() * sizeof(WorkItem), P.prefix.data(), P.prefix.size() * 4);
+    std::memcpy(dst + sizeof(h), items, (size_t)n * sizeof(WorkItem));
+    std::memcpy(dst + sizeof(h) + (size_t)n * sizeof(WorkItem), prefix, (size_t)(n + 1) * 4);
+}
+
+static void write_worklist(const Packed &P, uint8_t *dst)
+{
+    write_worklist_raw(P.items.data(), P.prefix.data(), (int)P.items.size(), P.info.total_tiles, dst);
 }
 
 // ---------------------------------------------------------------------------
@@ -343,8 +361,8 @@ static std::string class_key(const Packed &P, int n)
     cudaDeviceProp prop;
     cudaGetDeviceProperties(&prop, dev);
     const int nb = (int)std::floor(std::log2((double)std::max(n, 1)));
-    const int pb = (int)std::floor(std::log2(std::max(P.out_px, 1.0)));
-    std::snprintf(b, sizeof(b), "%s|n2^%d|px2^%d|ops%d", prop.name, nb, pb, P.opmask);
+    const int pb = (int)std::floor(std::log2(std::max(P.info.out_px, 1.0)));
+    std::snprintf(b, sizeof(b), "%s|n2^%d|px2^%d|ops%d", prop.name, nb, pb, P.info.opmask);
     return b;
 }
 
@@ -354,10 +372,10 @@ static kr_status enqueue(const Packed &P, void *ws, int cfg, int ctas_per_sm, bo
 {
     const size_t bytes = worklist_bytes((int)P.items.size());
     int occ = 1;
-    cudaError_t e = prepare_cfg(cfg, P.smem, occ);
+    cudaError_t e = prepare_cfg(cfg, P.info.smem, occ);
     if (e != cudaSuccess) { set_last_error(where, e); return KR_ERR_CUDA; }
     const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
-    const int grid = std::max(1, std::min(sm_count() * per_sm, P.total_tiles));
+    const int grid = std::max(1, std::min(sm_count() * per_sm, P.info.total_tiles));
 
     std::lock_guard<std::mutex> lk(g_mu);
     Ctx *c = nullptr;
@@ -373,11 +391,11 @@ static kr_status enqueue(const Packed &P, void *ws, int cfg, int ctas_per_sm, bo
         e = cudaMemcpyAsync(ws, c->slot[s], bytes, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess) {
             void *args[] = {&ws};
-            e = cudaLaunchKernel(g_cfgs[cfg].kernel, dim3(grid), dim3(kThreads), args, P.smem, stream);
+            e = cudaLaunchKernel(g_cfgs[cfg].kernel, dim3(grid), dim3(kThreads), args, P.info.smem, stream);
         }
     } else {
         char key[96];
-        std::snprintf(key, sizeof(key), "%p|%d|%d|%zu", (void *)stream, cfg, grid, P.smem);
+        std::snprintf(key, sizeof(key), "%p|%d|%d|%zu", (void *)stream, cfg, grid, P.info.smem);
         GraphEntry &g = c->graphs[key];
         if (!g.exec) {
             e = cudaGraphCreate(&g.graph, 0);
@@ -392,7 +410,7 @@ static kr_status enqueue(const Packed &P, void *ws, int cfg, int ctas_per_sm, bo
                 kp.func = (void *)g_cfgs[cfg].kernel;
                 kp.gridDim = dim3(grid);
                 kp.blockDim = dim3(kThreads);
-                kp.sharedMemBytes = (unsigned)P.smem;
+                kp.sharedMemBytes = (unsigned)P.info.smem;
                 kp.kernelParams = args;
                 e = cudaGraphAddKernelNode(&kn, g.graph, &g.copy, 1, &kp);
             }
@@ -412,6 +430,43 @@ static kr_status enqueue(const Packed &P, void *ws, int cfg, int ctas_per_sm, bo
     if (e == cudaSuccess) e = cudaEventRecord(c->done[s], stream);
     if (e != cudaSuccess) { set_last_error(where, e); return KR_ERR_CUDA; }
     return KR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free batch submit: the work list lives in a file-scope device
+// array instead of a caller workspace, and is copied there from a file-scope
+// host array, so the call allocates no device or host memory.
+// ---------------------------------------------------------------------------
+constexpr int kNoallocMaxItems = KR_BATCH_NOALLOC_MAX_ITEMS;
+constexpr size_t kNoallocBytes = worklist_bytes(kNoallocMaxItems);
+
+// Every device that loads the library holds this array until the process exits.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoallocBytes];
+
+static std::mutex g_noalloc_mu;                       // guards the host image below
+static uint8_t g_noalloc_host[kNoallocBytes];         // packed work list, host side
+static WorkItem g_noalloc_items[kNoallocMaxItems];
+static int g_noalloc_prefix[kNoallocMaxItems + 1];
+constexpr int kMaxDevices = 64;
+static void *g_noalloc_dev[kMaxDevices];              // device address of the array, per device
+
+// The device address of g_noalloc_scratch on the current device. The name of the
+// array is only a host-side stand-in; its address comes from cudaGetSymbolAddress,
+// asked once per device with that device current.
+static cudaError_t noalloc_scratch_ptr(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_noalloc_dev[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_dev[dev] = p;
+    }
+    *out = g_noalloc_dev[dev];
+    return cudaSuccess;
 }
 
 }  // namespace kr
@@ -464,9 +519,51 @@ kr_status kr_batch_submit(const kr_work_t *items, int32_t n, void *workspace, si
         return st;
     }
     // every item must fit in shared memory at this tile shape
-    if (P.smem > (size_t)g_cfgs[cfg].max_smem) return KR_ERR_UNSUPPORTED;
+    if (P.info.smem > (size_t)g_cfgs[cfg].max_smem) return KR_ERR_UNSUPPORTED;
     return enqueue(P, workspace, cfg, ctas, opts && opts->use_graph, (cudaStream_t)stream,
                    "kr_batch_submit");
+}
+
+kr_status kr_batch_submit_noalloc(const kr_work_t *items, int32_t n, const kr_batch_opts_t *opts,
+                                  kr_stream_t stream)
+{
+    if (n < 0 || (n > 0 && !items)) return KR_ERR_INVALID_ARG;
+    if (n == 0) return KR_OK;
+    if (n > kNoallocMaxItems) return KR_ERR_NO_SPACE;
+    const int cfg = (opts && opts->tile_config >= 0) ? opts->tile_config : 0;
+    const int ctas = opts ? opts->ctas_per_sm : 0;
+    if (cfg >= kNumCfgs || ctas < 0) return KR_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    PackInfo P;
+    kr_status st = pack_into(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th, g_noalloc_items, g_noalloc_prefix, P);
+    if (st != KR_OK) return st;
+    if (P.smem > (size_t)g_cfgs[cfg].max_smem) return KR_ERR_UNSUPPORTED;
+    int occ = 1;
+    void *ws = nullptr;
+    cudaError_t e = prepare_cfg(cfg, P.smem, occ);
+    if (e == cudaSuccess) e = noalloc_scratch_ptr(&ws);
+    if (e != cudaSuccess) {
+        set_last_error("kr_batch_submit_noalloc", e);
+        return KR_ERR_CUDA;
+    }
+    const int per_sm = ctas > 0 ? std::min(ctas, occ) : occ;
+    const int grid = std::max(1, std::min(sm_count() * per_sm, P.total_tiles));
+    const size_t bytes = worklist_bytes(n);
+    write_worklist_raw(g_noalloc_items, g_noalloc_prefix, n, P.total_tiles, g_noalloc_host);
+    // Pageable source: the call returns once the bytes are out of g_noalloc_host, so the
+    // next call may overwrite it. The copy also clears the header's tile counter.
+    e = cudaMemcpyAsync(ws, g_noalloc_host, bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        void *args[] = {&ws};
+        e = cudaLaunchKernel(g_cfgs[cfg].kernel, dim3(grid), dim3(kThreads), args, P.smem, s);
+    }
+    if (e != cudaSuccess) {
+        set_last_error("kr_batch_submit_noalloc", e);
+        return KR_ERR_CUDA;
+    }
+    return KR_OK;
 }
 
 kr_status kr_autotune_batch(const kr_work_t *items, int32_t n, void *workspace, size_t ws_bytes,
@@ -486,9 +583,9 @@ kr_status kr_autotune_batch(const kr_work_t *items, int32_t n, void *workspace, 
         kr_status st = pack_items(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th, P);
         if (st != KR_OK) { result = st; break; }
         if (cfg == 0) key = class_key(P, n);
-        if (P.smem > (size_t)g_cfgs[cfg].max_smem) continue;
+        if (P.info.smem > (size_t)g_cfgs[cfg].max_smem) continue;
         int occ = 1;
-        if (prepare_cfg(cfg, P.smem, occ) != cudaSuccess) { result = KR_ERR_CUDA; break; }
+        if (prepare_cfg(cfg, P.info.smem, occ) != cudaSuccess) { result = KR_ERR_CUDA; break; }
         for (int k = 1; k <= occ; ++k) {
             if (k > 2 && k < occ) continue;   // candidates: 1, 2 and the occupancy limit
             float ms_best = 1e30f;

@@ -3,7 +3,6 @@
 
 #include <cstddef>
 #include <cstdint>
-#include <string>
 
 #include <cuda_runtime.h>
 
@@ -68,6 +67,6 @@ kr_status build_resample(int op, const kr_image_t *src, const kr_image_t *dst, c
 kr_status build_gray(const kr_image_t *src, const kr_image_t *dst, GrayDesc &d);
 
 // Thread-local last CUDA error text.
-void set_last_error(const std::string &what, cudaError_t e);
+void set_last_error(const char *what, cudaError_t e);
 
 }  // namespace kr
