@@ -385,31 +385,23 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         }
     }
     __syncthreads();
-    if (tid == 0) {
-        const int cols = ti.fx1 - ti.fx0 + 1, rows = ti.fy1 - ti.fy0 + 1;
-        bool staged = cols >= 1 && rows >= 1 && J.foot_budget > 0;
-        const int srow = raw_row_bytes(max(cols, 1), CIN), sw = word_row(max(cols, 1));
-        if (staged) {
-            if (CIN == 3)
-                staged = (long long)rows * sw * 4 <= J.foot_budget && (long long)rows * srow <= J.region_b;
-            else
-                staged = (long long)rows * srow + 16 <= J.foot_budget;
-        }
-        ti.srow = srow;
-        ti.sw = sw;
-        ti.staged = staged;
-        ti.fast = (OP == OP_RESIZE ? 1 : ti.fast) && staged;   // resize taps always lie in the box
-    }
-    __syncthreads();
+    // Every thread derives the staging decision from the planned box (no extra barrier).
     const int fx0 = ti.fx0, fx1 = ti.fx1, fy0 = ti.fy0, fy1 = ti.fy1;
-    const int srow = ti.srow, sw = ti.sw;
-    const bool staged = ti.staged != 0, fast = ti.fast != 0;
+    const int rows = fy1 - fy0 + 1, cols = fx1 - fx0 + 1;
+    const int srow = raw_row_bytes(max(cols, 1), CIN), sw = word_row(max(cols, 1));
+    bool staged = cols >= 1 && rows >= 1 && J.foot_budget > 0;
+    if (staged) {
+        if (CIN == 3)
+            staged = (long long)rows * sw * 4 <= J.foot_budget && (long long)rows * srow <= J.region_b;
+        else
+            staged = (long long)rows * srow + 16 <= J.foot_budget;
+    }
+    const bool fast = staged && (OP == OP_RESIZE || ti.fast != 0);   // resize taps always lie in the box
     uint8_t *regA = smem;
     uint8_t *regB = smem + J.foot_budget;
     uint8_t *raw = CIN == 3 ? regB : regA;
     uint8_t *ostage = regB;
     const uint32_t *words = reinterpret_cast<const uint32_t *>(regA);
-    const int rows = fy1 - fy0 + 1, cols = fx1 - fx0 + 1;
 
     // ---- 2. stage ----------------------------------------------------------------
     if (staged) {
@@ -418,25 +410,27 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         // [ibeg, iend) so that every read stays inside the described buffer; bytes
         // between rows (pitch padding) may be read but are never used. Only a chunk
         // cut by ibeg or iend (the image's first or last 16 bytes) goes byte by byte.
+        // The (row, chunk) pairs are spread over the whole CTA.
         const int L = cols * CIN;
+        const int nchr = (L + 15 + 15) >> 4;                 // chunks a row can span
+        const float inv_nchr = __frcp_rn((float)nchr);
         const uintptr_t ibeg = (uintptr_t)J.src;
         const uintptr_t iend = (uintptr_t)(J.src + (int64_t)(J.H - 1) * J.spitch + (int64_t)J.W * CIN);
-        for (int r = warp; r < rows; r += kWarps) {
-            const uintptr_t a = (uintptr_t)(J.src + (int64_t)(fy0 + r) * J.spitch + (int64_t)fx0 * CIN);
+        const uint8_t *row0 = J.src + (int64_t)fy0 * J.spitch + (int64_t)fx0 * CIN;
+        for (int i = tid; i < rows * nchr; i += kThreads) {
+            const int r = (int)__fmul_rz((float)i + 0.5f, inv_nchr);   // i / nchr (exact: i < 2^16)
+            const int j = i - r * nchr;
+            const uintptr_t a = (uintptr_t)(row0 + (int64_t)r * J.spitch);
             const uintptr_t G = a & ~(uintptr_t)15;
-            const uintptr_t lo = G > ibeg ? G : ibeg;
+            const uintptr_t c0 = G + 16 * (uintptr_t)j;
             const uintptr_t e16 = (a + L + 15) & ~(uintptr_t)15;
-            const uintptr_t hi = e16 < iend ? e16 : iend;
-            const int nch = (int)((e16 - G) >> 4);
-            uint8_t *srowp = raw + r * srow;
-            for (int j = lane; j < nch; j += 32) {
-                const uintptr_t c0 = G + 16 * (uintptr_t)j;
-                if (c0 >= lo && c0 + 16 <= hi) {
-                    cp_async16(srowp + 16 * j, reinterpret_cast<const void *>(c0));
-                } else {
-                    const uintptr_t b0 = c0 > lo ? c0 : lo, b1 = (c0 + 16 < hi) ? c0 + 16 : hi;
-                    for (uintptr_t b = b0; b < b1; ++b) srowp[b - G] = __ldg(reinterpret_cast<const uint8_t *>(b));
-                }
+            if (c0 >= e16) continue;
+            uint8_t *dstp = raw + r * srow + 16 * j;
+            if (c0 >= ibeg && c0 + 16 <= iend) {
+                cp_async16(dstp, reinterpret_cast<const void *>(c0));
+            } else {
+                const uintptr_t b0 = c0 > ibeg ? c0 : ibeg, b1 = (c0 + 16 < iend) ? c0 + 16 : iend;
+                for (uintptr_t b = b0; b < b1; ++b) dstp[b - c0] = __ldg(reinterpret_cast<const uint8_t *>(b));
             }
         }
         cp_async_wait_all();
@@ -444,11 +438,13 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         if (CIN == 3) {
             // Re-lay each row as one word per pixel, 4 pixels (12 bytes) per step.
             const int gpr = (cols + 3) >> 2;
-            const uint32_t rowphase0 = (uint32_t)(uintptr_t)(J.src + (int64_t)fx0 * 3);
+            const float inv_gpr = __frcp_rn((float)gpr);
+            const uint32_t rowphase0 = (uint32_t)(uintptr_t)row0;
+            const uint32_t sp = (uint32_t)J.spitch;
             for (int i = tid; i < rows * gpr; i += kThreads) {
-                const int r = i / gpr, g = i - r * gpr;
-                const int ph = (int)((rowphase0 + (uint32_t)((int64_t)(fy0 + r) * J.spitch)) & 15u);
-                const int o = ph + 12 * g;
+                const int r = (int)__fmul_rz((float)i + 0.5f, inv_gpr);
+                const int g = i - r * gpr;
+                const int o = (int)((rowphase0 + (uint32_t)r * sp) & 15u) + 12 * g;
                 const uint32_t *wp = reinterpret_cast<const uint32_t *>(raw + r * srow + (o & ~3));
                 const uint32_t sh = (uint32_t)(o & 3) * 8u;
                 const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2], w3 = wp[3];
@@ -608,28 +604,54 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     }
     __syncthreads();
 
-    // ---- 4. write-out: one warp per (plane, row); 16-byte chunks for the aligned
-    // body, one byte per lane for the (at most 15 + 15) head and tail bytes.
+    // ---- 4. write-out: 16-byte chunks of every (plane, row) segment spread over the
+    // CTA; a second pass, only when some row is not 16-byte aligned at both ends,
+    // moves the (at most 15 + 15) head and tail bytes of each segment, one per thread.
     const int nplanes = chw ? 3 : 1;
     const int seglen = chw ? nx * 4 : nx * dC * ES;
-    for (int s = warp; s < nplanes * ny; s += kWarps) {
-        const int pl = s / ny, r = s - pl * ny;
-        uint8_t *g = J.dst + (int64_t)(ty0 + r) * J.dpitch +
-                     (chw ? (int64_t)pl * J.dplane + (int64_t)tx0 * 4 : (int64_t)tx0 * dC * ES);
+    const int nseg = nplanes * ny;
+    const int ncs = (seglen + 15 + 15) >> 4;           // chunks a segment can span
+    const float inv_ncs = __frcp_rn((float)ncs);
+    const int64_t tile_off = chw ? (int64_t)tx0 * 4 : (int64_t)tx0 * dC * ES;
+    uint8_t *drow0 = J.dst + (int64_t)ty0 * J.dpitch + tile_off;
+    auto seg_base = [&](int sidx, int &r) -> uint8_t * {
+        const int pl = chw ? (sidx >= ny) + (sidx >= 2 * ny) : 0;
+        r = sidx - pl * ny;
+        return drow0 + (int64_t)r * J.dpitch + (int64_t)pl * J.dplane;
+    };
+    for (int i = tid; i < nseg * ncs; i += kThreads) {
+        const int sidx = (int)__fmul_rz((float)i + 0.5f, inv_ncs);
+        const int j = i - sidx * ncs;
+        int r;
+        uint8_t *g = seg_base(sidx, r);
         const int phase = (int)((uintptr_t)g & 15);
-        uint8_t *G = g - phase;
-        const uint8_t *S = ostage + (pl * TH + r) * orow;
-        const int end = phase + seglen;
-        const int jf = (phase + 15) >> 4, jl = end >> 4;   // full chunks: [jf, jl)
-        for (int j = jf + lane; j < jl; j += 32)
-            *reinterpret_cast<uint4 *>(G + 16 * j) = *reinterpret_cast<const uint4 *>(S + 16 * j);
-        const int head_end = min(jf * 16, end);
-        if (lane < 16) {
-            const int b = phase + lane;
-            if (b < head_end) G[b] = S[b];
-        } else if (jl >= jf) {
-            const int b = jl * 16 + (lane - 16);
-            if (b < end) G[b] = S[b];
+        const int b0 = 16 * j;
+        if (b0 >= phase && b0 + 16 <= phase + seglen) {
+            const int pl = chw ? (sidx >= ny) + (sidx >= 2 * ny) : 0;
+            *reinterpret_cast<uint4 *>(g - phase + b0) =
+                *reinterpret_cast<const uint4 *>(ostage + (pl * TH + r) * orow + b0);
+        }
+    }
+    const bool aligned_rows = ((obase | opitch | (chw ? oplane : 0u) | (uint32_t)seglen) & 15u) == 0;
+    if (!aligned_rows) {
+        for (int i = tid; i < nseg * 32; i += kThreads) {
+            const int sidx = i >> 5, k = i & 31;
+            int r;
+            uint8_t *g = seg_base(sidx, r);
+            const int pl = chw ? (sidx >= ny) + (sidx >= 2 * ny) : 0;
+            const int phase = (int)((uintptr_t)g & 15);
+            const int end = phase + seglen;
+            const int jf = (phase + 15) >> 4, jl = end >> 4;   // full chunks: [jf, jl)
+            int b;
+            if (k < 16) {
+                b = phase + k;
+                if (b >= min(jf * 16, end)) continue;
+            } else {
+                if (jl < jf) continue;
+                b = jl * 16 + (k - 16);
+                if (b >= end) continue;
+            }
+            g[b - phase] = ostage[(pl * TH + r) * orow + b];
         }
     }
     __syncthreads();
