@@ -220,4 +220,17 @@ const char *kr_status_string(kr_status s)
 
 const char *kr_last_error(void) { return g_last_error; }
 
+kr_status kr_device_errors(uint32_t *flags, int32_t clear)
+{
+    if (!flags) return KR_ERR_INVALID_ARG;
+    unsigned v = 0;
+    cudaError_t e = device_error_flags(&v, clear != 0);
+    if (e != cudaSuccess) {
+        set_last_error("kr_device_errors", e);
+        return KR_ERR_CUDA;
+    }
+    *flags = v;
+    return KR_OK;
+}
+
 }  // extern "C"

@@ -92,6 +92,11 @@ __device__ __forceinline__ Job job_of(const WorkItem &it)
     J.foot_budget = it.foot_budget;
     J.region_b = it.region_b;
     J.allow_fast = it.allow_fast;
+    J.tin = nullptr;
+    J.tin_nc = J.tin_br = 0;
+    J.tout = nullptr;
+    J.zimg = 0;
+    J.err = nullptr;
 #pragma unroll
     for (int k = 0; k < 6; ++k) J.M[k] = it.M[k];
 #pragma unroll
@@ -105,7 +110,7 @@ __device__ __forceinline__ Job job_of(const WorkItem &it)
 template <int TW, int TH>
 __global__ void __launch_bounds__(kThreads) ragged_kernel(uint8_t *ws)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     __shared__ TileShared<TW, TH> ts;
     __shared__ int s_tile;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);

@@ -30,6 +30,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace kr {
@@ -53,6 +54,13 @@ struct Job {
     int32_t foot_budget;  // shared bytes of region A (staged box); 0 = never stage
     int32_t region_b;     // shared bytes of region B (raw rows of 3-channel boxes, then output tile)
     int32_t allow_fast;   // warp: the map's intermediate terms are small enough for the fast path
+    // TMA (per-operation kernels; null in the ragged kernel). Both maps view images as
+    // {16 bytes, 16-byte chunk, row, (plane,) image} tensors.
+    const CUtensorMap *tin;   // source map, box {16, tin_nc, tin_br, 1}; null = cp.async staging
+    int32_t tin_nc, tin_br;
+    const CUtensorMap *tout;  // destination map, box = one output tile; null = 128-bit stores
+    int32_t zimg;             // image coordinate of this job in both maps
+    unsigned *err;            // device error flags (bit 0: a bounded TMA wait ran out)
     float M[6];           // destination -> source map (warp)
     float scale[3];       // f32: out = v255 * scale[c] + bias[c]
     float bias[3];
@@ -183,6 +191,90 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// ---------------------------------------------------------------------------
+// TMA and mbarrier helpers (sm_90+ PTX, used here on sm_103a)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t *mbar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n"
+                 "fence.mbarrier_init.release.cluster;\n" ::"r"(smem_addr(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(smem_addr(mbar)), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the mbarrier phase `parity`, giving up after `limit_ns` nanoseconds.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parity, uint64_t limit_ns)
+{
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(mbar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
+// 4-D tensor load {c0, c1, c2, c3} of the map's box into shared memory, completing on mbar.
+__device__ __forceinline__ void tma_load_4d(void *sdst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *mbar)
+{
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_addr(sdst)),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, int c0, int c1, int c2, int c3, const void *ssrc)
+{
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(ssrc))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
+                                             const void *ssrc)
+{
+    asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(ssrc))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_store_commit_and_wait_read()
+{
+    asm volatile("cp.async.bulk.commit_group;\ncp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+
+// Make this thread's generic-proxy shared-memory writes visible to the TMA (async proxy).
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// Bound of every TMA wait: far above any copy's latency, far below a hang.
+constexpr uint64_t kTmaWaitNs = 2000000000ull;
+
 // One RGB pixel from global memory as a word R | G << 8 | B << 16 (zero outside the image).
 __device__ __forceinline__ uint32_t ldg_px3(const uint8_t *src, int64_t spitch, int H, int W, int y,
                                             int x)
@@ -243,9 +335,11 @@ struct TileInfo {
     int staged;               // the box is in shared memory
     int fast;                 // every tap of the tile is inside the box (and, for warp,
                               // every coordinate lies in [0, 4094))
+    int tma_ok;               // the TMA copy of the box completed
 };
 
 template <int TW, int TH> struct TileShared {
+    uint64_t mbar;   // completion barrier of the box's TMA copy
     TileInfo ti;
     int cx0[TW];     // column tap x0
     int cqd[TW];     // q | (x1 - x0) << 16
@@ -397,6 +491,10 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             staged = (long long)rows * srow + 16 <= J.foot_budget;
     }
     const bool fast = staged && (OP == OP_RESIZE || ti.fast != 0);   // resize taps always lie in the box
+    // TMA staging when the launch has a source map whose box holds this tile's box.
+    const bool use_tma = staged && J.tin != nullptr && rows <= J.tin_br &&
+                         ((fx0 * CIN) & 15) + cols * CIN <= 16 * J.tin_nc;
+    const int rstride = use_tma ? 16 * J.tin_nc : srow;   // bytes between staged raw rows
     uint8_t *regA = smem;
     uint8_t *regB = smem + J.foot_budget;
     uint8_t *raw = CIN == 3 ? regB : regA;
@@ -412,11 +510,27 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         // cut by ibeg or iend (the image's first or last 16 bytes) goes byte by byte.
         // The (row, chunk) pairs are spread over the whole CTA.
         const int L = cols * CIN;
+        const uint8_t *row0 = J.src + (int64_t)fy0 * J.spitch + (int64_t)fx0 * CIN;
+        if (use_tma) {
+            // One TMA copy of the box: rows fy0.., 16-byte chunks from the one holding byte
+            // fx0*CIN of each row (rows are 16-byte aligned, so every row has the same phase).
+            if (tid == 0) {
+                mbar_init(&ts.mbar);
+                mbar_expect_tx(&ts.mbar, (uint32_t)(16 * J.tin_nc * J.tin_br));
+                tma_load_4d(raw, J.tin, 0, (fx0 * CIN) >> 4, fy0, J.zimg, &ts.mbar);
+                ti.tma_ok = mbar_wait_bounded(&ts.mbar, 0, kTmaWaitNs) ? 1 : 0;
+                if (!ti.tma_ok) {
+                    atomicOr(J.err, 1u);
+                    mbar_wait_bounded(&ts.mbar, 0, kTmaWaitNs);   // let the copy land before leaving
+                }
+            }
+            __syncthreads();
+            if (!ti.tma_ok) return;
+        } else {
         const int nchr = (L + 15 + 15) >> 4;                 // chunks a row can span
         const float inv_nchr = __frcp_rn((float)nchr);
         const uintptr_t ibeg = (uintptr_t)J.src;
         const uintptr_t iend = (uintptr_t)(J.src + (int64_t)(J.H - 1) * J.spitch + (int64_t)J.W * CIN);
-        const uint8_t *row0 = J.src + (int64_t)fy0 * J.spitch + (int64_t)fx0 * CIN;
         for (int i = tid; i < rows * nchr; i += kThreads) {
             const int r = (int)__fmul_rz((float)i + 0.5f, inv_nchr);   // i / nchr (exact: i < 2^16)
             const int j = i - r * nchr;
@@ -425,7 +539,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             const uintptr_t c0 = G + 16 * (uintptr_t)j;
             const uintptr_t e16 = (a + L + 15) & ~(uintptr_t)15;
             if (c0 >= e16) continue;
-            uint8_t *dstp = raw + r * srow + 16 * j;
+            uint8_t *dstp = raw + r * rstride + 16 * j;
             if (c0 >= ibeg && c0 + 16 <= iend) {
                 cp_async16(dstp, reinterpret_cast<const void *>(c0));
             } else {
@@ -435,6 +549,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         }
         cp_async_wait_all();
         __syncthreads();
+        }
         if (CIN == 3) {
             // Re-lay each row as one word per pixel, 4 pixels (12 bytes) per step.
             const int gpr = (cols + 3) >> 2;
@@ -445,7 +560,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                 const int r = (int)__fmul_rz((float)i + 0.5f, inv_gpr);
                 const int g = i - r * gpr;
                 const int o = (int)((rowphase0 + (uint32_t)r * sp) & 15u) + 12 * g;
-                const uint32_t *wp = reinterpret_cast<const uint32_t *>(raw + r * srow + (o & ~3));
+                const uint32_t *wp = reinterpret_cast<const uint32_t *>(raw + r * rstride + (o & ~3));
                 const uint32_t sh = (uint32_t)(o & 3) * 8u;
                 const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2], w3 = wp[3];
                 const uint32_t b0 = __funnelshift_r(w0, w1, sh);
@@ -464,7 +579,10 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
 
     // ---- 3. compute --------------------------------------------------------------
     const bool chw = OT::is_f32 && dC == 3 && J.chw;
-    const int orow = chw ? round16(TW * 4 + 15) : round16(TW * dC * ES + 15);
+    // output rows: dense when the tile leaves through a TMA store (its rows are 16-byte
+    // aligned), else with room for each row's 16-byte phase
+    const bool tma_out = J.tout != nullptr;
+    const int orow = tma_out ? (chw ? TW * 4 : TW * dC * ES) : (chw ? round16(TW * 4 + 15) : round16(TW * dC * ES + 15));
     // low address bits of output row 0 of the tile (plane 0): staging rows keep their phase
     const uint32_t obase = (uint32_t)(uintptr_t)(J.dst + (int64_t)ty0 * J.dpitch +
                                                  (chw ? (int64_t)tx0 * 4 : (int64_t)tx0 * dC * ES));
@@ -583,8 +701,8 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                         const int r0 = y0 - fy0, r1 = r0 + dy;
                         const int ph0 = (int)((rowphase0 + (uint32_t)((int64_t)y0 * J.spitch)) & 15u);
                         const int ph1 = (int)((rowphase0 + (uint32_t)((int64_t)(y0 + dy) * J.spitch)) & 15u);
-                        const uint8_t *s0 = raw + r0 * srow + ph0 + (x0 - fx0);
-                        const uint8_t *s1 = raw + r1 * srow + ph1 + (x0 - fx0);
+                        const uint8_t *s0 = raw + r0 * rstride + ph0 + (x0 - fx0);
+                        const uint8_t *s1 = raw + r1 * rstride + ph1 + (x0 - fx0);
                         p00 = s0[0]; p01 = s0[dx]; p10 = s1[0]; p11 = s1[dx];
                     } else if (CIN == 3) {
                         p00 = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0);
@@ -602,7 +720,24 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             }
         }
     }
+    if (tma_out) fence_proxy_async_smem();
     __syncthreads();
+
+    if (tma_out) {
+        // ---- 4. write-out through TMA stores of the whole tile (rows and chunks past the
+        // image's edge are clipped by the copy engine).
+        if (tid == 0) {
+            if (chw) {
+                for (int pl = 0; pl < 3; ++pl)
+                    tma_store_5d(J.tout, 0, tx0 >> 2, ty0, pl, J.zimg, ostage + pl * TH * orow);
+            } else {
+                tma_store_4d(J.tout, 0, (tx0 * dC * ES) >> 4, ty0, J.zimg, ostage);
+            }
+            tma_store_commit_and_wait_read();
+        }
+        __syncthreads();
+        return;
+    }
 
     // ---- 4. write-out: 16-byte chunks of every (plane, row) segment spread over the
     // CTA; a second pass, only when some row is not 16-byte aligned at both ends,

@@ -53,6 +53,7 @@ cudaError_t launch_gray(const GrayDesc &d, cudaStream_t stream);
 struct Budget {
     int a;
     int b;
+    int cols, rows;   // bound of a tile's source box (pixels), clipped to the image
 };
 Budget budget_resize(int cin, int H, int W, int h, int w, int tw, int th, int out_bytes);
 Budget budget_warp(int cin, int H, int W, const float *M, int tw, int th, int out_bytes);
@@ -60,6 +61,9 @@ Budget budget_warp(int cin, int H, int W, const float *M, int tw, int th, int ou
 // every intermediate of the fp32 coordinate below 2^20, so interior pixels deviate from the
 // corner hull by far less than the box margin: such maps may use the fast tile path.
 bool warp_allows_fast(const float *M, int h, int w);
+
+// Device error flags of the per-operation kernels (synchronous read, optional clear).
+cudaError_t device_error_flags(unsigned *flags, bool clear);
 
 // Validation + descriptor construction (kr_abi.cu); nothing is enqueued.
 kr_status build_resample(int op, const kr_image_t *src, const kr_image_t *dst, const kr_post_t *post,

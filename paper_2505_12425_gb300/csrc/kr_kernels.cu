@@ -4,6 +4,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+
+#include <cudaTypedefs.h>
 
 #include "kr_device.cuh"
 #include "kr_internal.h"
@@ -14,7 +17,14 @@ namespace kr {
 constexpr int kTW = 64;
 constexpr int kTH = 32;
 
+// Device error flags of the per-operation kernels (bit 0: a bounded TMA wait ran out).
+static __device__ unsigned g_kr_device_err;
+
 struct OpParams {
+    CUtensorMap tin;    // source map (valid when has_tin)
+    CUtensorMap tout;   // destination map (valid when has_tout)
+    int32_t has_tin, has_tout;
+    int32_t tin_nc, tin_br;
     const uint8_t *src;
     int64_t spitch, sbatch;
     int32_t H, W;
@@ -32,7 +42,7 @@ struct OpParams {
 template <int OP, int CIN, int OUTK, int TW, int TH>
 __global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constant__ OpParams p)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
+    extern __shared__ __align__(128) uint8_t smem[];
     __shared__ TileShared<TW, TH> ts;
     const int z = blockIdx.z;
     Job J;
@@ -49,6 +59,12 @@ __global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constan
     J.foot_budget = p.foot_budget;
     J.region_b = p.region_b;
     J.allow_fast = OP == OP_WARP ? (int)((p.fast_mask[z >> 5] >> (z & 31)) & 1u) : 1;
+    J.tin = p.has_tin ? &p.tin : nullptr;
+    J.tin_nc = p.tin_nc;
+    J.tin_br = p.tin_br;
+    J.tout = p.has_tout ? &p.tout : nullptr;
+    J.zimg = z;
+    J.err = &g_kr_device_err;
 #pragma unroll
     for (int k = 0; k < 6; ++k) J.M[k] = OP == OP_WARP ? p.M[z][k] : 0.f;
 #pragma unroll
@@ -62,6 +78,8 @@ __global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constan
 // ---------------------------------------------------------------------------
 // Shared-memory budgets
 // ---------------------------------------------------------------------------
+static int round128(int x) { return (x + 127) & ~127; }
+
 static Budget budget_for(int cin, double cols_d, double rows_d, int H, int W, int out_bytes, bool clamp)
 {
     const int cols = (int)std::min<double>(cols_d, W), rows = (int)std::min<double>(rows_d, H);
@@ -74,8 +92,10 @@ static Budget budget_for(int cin, double cols_d, double rows_d, int H, int W, in
         raw = 0;
     }
     Budget b;
+    b.cols = cols;
+    b.rows = rows;
     if (a <= kFootCap && raw <= kRegionBCap) {
-        b.a = round16((int)a);
+        b.a = round128((int)a);
         b.b = round16((int)std::max<long long>(out_bytes, raw));
     } else if (clamp) {
         // tiles whose box fits these caps are staged, the others take the general path
@@ -115,6 +135,56 @@ bool warp_allows_fast(const float *M, int h, int w)
             return false;
     }
     return true;
+}
+
+// ---------------------------------------------------------------------------
+// TMA tensor maps: images as {16 bytes, 16-byte chunk, row, (plane,) image} tensors
+// ---------------------------------------------------------------------------
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Map over n images of `rows` rows whose first `rowbytes` bytes are used, with an extra
+// plane dimension when planes > 1. Box: {16, box_chunks, box_rows, 1(, 1)}. Returns false
+// (and the caller keeps the non-TMA path) when the layout does not meet TMA's rules.
+static bool encode_map(CUtensorMap *m, const void *base, int64_t rowbytes, int rows, int planes, int n,
+                       int64_t pitch, int64_t pstride, int64_t bstride, int box_chunks, int box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const int64_t nchunk = (rowbytes + 15) / 16;
+    if (((uintptr_t)base & 15) || (pitch & 15) || pitch < nchunk * 16) return false;
+    if (box_chunks < 1 || box_chunks > 256 || box_rows < 1 || box_rows > 256) return false;
+    const int64_t pe = planes > 1 ? pstride : (int64_t)rows * pitch;          // plane extent
+    const int64_t be = n > 1 ? bstride : (planes > 1 ? planes * pstride : (int64_t)rows * pitch);
+    if (planes > 1 && ((pe & 15) || pe < (int64_t)rows * pitch)) return false;
+    if (n > 1 && ((be & 15) || be < (planes > 1 ? planes * pe : (int64_t)rows * pitch))) return false;
+    cuuint64_t dims[5];
+    cuuint64_t strides[4];
+    cuuint32_t box[5], es[5] = {1, 1, 1, 1, 1};
+    int rank = 0;
+    dims[rank] = 16; box[rank] = 16; ++rank;
+    dims[rank] = (cuuint64_t)nchunk; box[rank] = (cuuint32_t)box_chunks; strides[rank - 1] = 16; ++rank;
+    dims[rank] = (cuuint64_t)rows; box[rank] = (cuuint32_t)box_rows; strides[rank - 1] = (cuuint64_t)pitch; ++rank;
+    if (planes > 1) {
+        dims[rank] = (cuuint64_t)planes; box[rank] = 1; strides[rank - 1] = (cuuint64_t)pe; ++rank;
+    }
+    dims[rank] = (cuuint64_t)n; box[rank] = 1; strides[rank - 1] = (cuuint64_t)((be + 15) & ~(int64_t)15); ++rank;
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, rank, const_cast<void *>(base), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 // ---------------------------------------------------------------------------
@@ -176,6 +246,28 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
         p.region_b = bud.b;
         p.src = d.src + (int64_t)b0 * d.sbatch;
         p.dst = d.dst + (int64_t)b0 * d.dbatch;
+        // TMA source map: one box per tile covering the largest source box of the launch
+        p.has_tin = 0;
+        if (bud.a > 0) {
+            const int nc = (15 + bud.cols * CIN + 15) / 16, br = bud.rows;
+            const long long cap = CIN == 3 ? bud.b : bud.a - 16;
+            if ((long long)16 * nc * br <= cap &&
+                encode_map(&p.tin, p.src, (int64_t)d.W * CIN, d.H, 1, nb, d.spitch, 0, d.sbatch, nc, br)) {
+                p.has_tin = 1;
+                p.tin_nc = nc;
+                p.tin_br = br;
+            }
+        }
+        // TMA destination map: whole tiles, when every row is a whole number of 16-byte chunks
+        p.has_tout = 0;
+        constexpr int dC = OutTraits<OUTK, CIN>::dC, ES = OutTraits<OUTK, CIN>::esize;
+        const bool chw = d.chw != 0;
+        const int64_t orowb = chw ? (int64_t)d.w * 4 : (int64_t)d.w * dC * ES;
+        if (orowb % 16 == 0) {
+            const int tile_chunks = chw ? TW * 4 / 16 : TW * dC * ES / 16;
+            p.has_tout = encode_map(&p.tout, p.dst, orowb, d.h, chw ? 3 : 1, nb, d.dpitch, d.dplane, d.dbatch,
+                                    tile_chunks, TH) ? 1 : 0;
+        }
         const size_t smem = (size_t)bud.a + bud.b;
         dim3 grid(tiles_x, tiles_y, nb);
         kern<<<grid, kThreads, smem, stream>>>(p);
@@ -260,6 +352,16 @@ __global__ void __launch_bounds__(kThreads) gray_kernel(const __grid_constant__ 
                 d[k] = (uint8_t)gray_u8(__ldg(s + 3 * k), __ldg(s + 3 * k + 1), __ldg(s + 3 * k + 2));
         }
     }
+}
+
+cudaError_t device_error_flags(unsigned *flags, bool clear)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(flags, g_kr_device_err, sizeof(unsigned));
+    if (e == cudaSuccess && clear) {
+        const unsigned zero = 0;
+        e = cudaMemcpyToSymbol(g_kr_device_err, &zero, sizeof(unsigned));
+    }
+    return e;
 }
 
 cudaError_t launch_gray(const GrayDesc &d, cudaStream_t stream)
