@@ -336,6 +336,7 @@ struct TileInfo {
     int fast;                 // every tap of the tile is inside the box (and, for warp,
                               // every coordinate lies in [0, 4094))
     int tma_ok;               // the TMA copy of the box completed
+    int zero;                 // warp: the box misses the image, every sample is 0
 };
 
 template <int TW, int TH> struct TileShared {
@@ -465,17 +466,19 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         }
         const bool all_ok = __all_sync(0xffffffffu, ok);
         if (lane == 0) {
-            int fx0 = 0, fx1 = -1, fy0 = 0, fy1 = -1, fast = 0;
+            // The box is NOT clipped to the image: staging fills its part outside the
+            // image with zeros, which is the zero border, so every tap reads the box.
+            int fx0 = 0, fx1 = -1, fy0 = 0, fy1 = -1, fast = 0, zero = 0;
             if (all_ok) {
-                const int ax0 = (int)floorf(mnx) - 1, ax1 = (int)floorf(mxx) + 3;
-                const int ay0 = (int)floorf(mny) - 1, ay1 = (int)floorf(mxy) + 3;
-                fx0 = max(ax0, 0); fx1 = min(ax1, J.W - 1);
-                fy0 = max(ay0, 0); fy1 = min(ay1, J.H - 1);
-                fast = J.allow_fast && fx0 == ax0 && fx1 == ax1 && fy0 == ay0 && fy1 == ay1 &&
-                       mxx < 4093.f && mxy < 4093.f;
+                fx0 = (int)floorf(mnx) - 1; fx1 = (int)floorf(mxx) + 3;
+                fy0 = (int)floorf(mny) - 1; fy1 = (int)floorf(mxy) + 3;
+                zero = fx1 < 0 || fx0 > J.W - 1 || fy1 < 0 || fy0 > J.H - 1;
+                // the one-fma weight form needs every coordinate in [0, 4094)
+                fast = J.allow_fast && mnx >= 1.f && mny >= 1.f && mxx < 4093.f && mxy < 4093.f;
             }
             ti.fx0 = fx0; ti.fx1 = fx1; ti.fy0 = fy0; ti.fy1 = fy1;
             ti.fast = fast;
+            ti.zero = zero;
         }
     }
     __syncthreads();
@@ -483,7 +486,8 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     const int fx0 = ti.fx0, fx1 = ti.fx1, fy0 = ti.fy0, fy1 = ti.fy1;
     const int rows = fy1 - fy0 + 1, cols = fx1 - fx0 + 1;
     const int srow = raw_row_bytes(max(cols, 1), CIN), sw = word_row(max(cols, 1));
-    bool staged = cols >= 1 && rows >= 1 && J.foot_budget > 0;
+    const bool zero_tile = OP == OP_WARP && ti.zero != 0;
+    bool staged = !zero_tile && cols >= 1 && rows >= 1 && J.foot_budget > 0;
     if (staged) {
         if (CIN == 3)
             staged = (long long)rows * sw * 4 <= J.foot_budget && (long long)rows * srow <= J.region_b;
@@ -526,6 +530,17 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             }
             __syncthreads();
             if (!ti.tma_ok) return;
+            if (OP == OP_WARP && ((J.W * CIN) & 15)) {
+                // rows end inside their last 16-byte chunk: the bytes after the last pixel
+                // are not image bytes, zero them (the copy engine filled only whole chunks)
+                const int xb0 = ((fx0 * CIN) >> 4) * 16;       // row offset of the box's first byte
+                const int z0 = J.W * CIN - xb0, z1 = ((J.W * CIN + 15) & ~15) - xb0;
+                if (z1 > 0 && z0 < 16 * J.tin_nc) {
+                    for (int r = tid; r < rows; r += kThreads)
+                        for (int b = max(z0, 0); b < min(z1, 16 * J.tin_nc); ++b) raw[r * rstride + b] = 0;
+                }
+                __syncthreads();
+            }
         } else {
         const int nchr = (L + 15 + 15) >> 4;                 // chunks a row can span
         const float inv_nchr = __frcp_rn((float)nchr);
@@ -540,11 +555,27 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             const uintptr_t e16 = (a + L + 15) & ~(uintptr_t)15;
             if (c0 >= e16) continue;
             uint8_t *dstp = raw + r * rstride + 16 * j;
-            if (c0 >= ibeg && c0 + 16 <= iend) {
+            uintptr_t lo = ibeg, hi = iend;   // bytes that may be read
+            if (OP == OP_WARP) {
+                // warp boxes may cross the image border: only the row's own pixels are
+                // read, everything else is the zero border
+                const int yi = fy0 + r;
+                if (yi < 0 || yi >= J.H) {
+                    *reinterpret_cast<uint4 *>(dstp) = make_uint4(0u, 0u, 0u, 0u);
+                    continue;
+                }
+                lo = (uintptr_t)(J.src + (int64_t)yi * J.spitch);
+                hi = lo + (uintptr_t)J.W * CIN;
+            }
+            if (c0 >= lo && c0 + 16 <= hi) {
                 cp_async16(dstp, reinterpret_cast<const void *>(c0));
+            } else if (c0 + 16 <= lo || c0 >= hi) {
+                *reinterpret_cast<uint4 *>(dstp) = make_uint4(0u, 0u, 0u, 0u);
             } else {
-                const uintptr_t b0 = c0 > ibeg ? c0 : ibeg, b1 = (c0 + 16 < iend) ? c0 + 16 : iend;
-                for (uintptr_t b = b0; b < b1; ++b) dstp[b - c0] = __ldg(reinterpret_cast<const uint8_t *>(b));
+                for (int k = 0; k < 16; ++k) {
+                    const uintptr_t b = c0 + k;
+                    dstp[k] = (b >= lo && b < hi) ? __ldg(reinterpret_cast<const uint8_t *>(b)) : (uint8_t)0;
+                }
             }
         }
         cp_async_wait_all();
@@ -600,7 +631,17 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         return o;
     };
 
-    if (fast && CIN == 3) {
+    if (zero_tile) {
+        // every tap lies outside the image: every output pixel is the zero sample
+        for (int r = warp; r < ny; r += kWarps) {
+            const ORow o = orow_of(r);
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                const int c = lane + 32 * j;
+                if (c < nx) emit<CIN, OUTK>(J, o, c, 0u, 0u, 0u, 0u, 0, 0, 0.f, 0.f);
+            }
+        }
+    } else if (fast && CIN == 3) {
         const int wbase = -(fy0 * sw + fx0);
         if (OP == OP_RESIZE) {
             int xo[CPL], xo1[CPL], qxs[CPL];   // word offsets of the two column taps in a box row
@@ -660,6 +701,34 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                         const uint32_t *w0 = words + (y0 * sw + x0 + wbase);
                         emit<CIN, OUTK>(J, o, c, w0[0], w0[1], w0[sw], w0[sw + 1], qx, qy, fx, fy);
                     }
+                }
+            }
+        }
+    } else if (OP == OP_WARP && CIN == 3 && staged) {
+        // Medium path (warp tiles with coordinates outside [0, 4094)): the exact weight
+        // formula per pixel; every tap still lies in the zero-filled box.
+        for (int r = warp; r < ny; r += kWarps) {
+            const float yc = __fadd_rn((float)(ty0 + r), 0.5f);
+            const float rx = __fmaf_rn(J.M[1], yc, J.M[2]);
+            const float ry = __fmaf_rn(J.M[4], yc, J.M[5]);
+            const ORow o = orow_of(r);
+#pragma unroll
+            for (int j = 0; j < CPL; ++j) {
+                const int c = lane + 32 * j;
+                if (c < nx) {
+                    const float xc = __fadd_rn((float)(tx0 + c), 0.5f);
+                    const float sx = __fsub_rn(__fmaf_rn(J.M[0], xc, rx), 0.5f);
+                    const float sy = __fsub_rn(__fmaf_rn(J.M[3], xc, ry), 0.5f);
+                    int x0, y0, qx, qy;
+                    warp_weight(sx, x0, qx);
+                    warp_weight(sy, y0, qy);
+                    float fx = 0.f, fy = 0.f;
+                    if (OT::is_f32) {
+                        fx = __fsub_rn(sx, floorf(sx));
+                        fy = __fsub_rn(sy, floorf(sy));
+                    }
+                    const uint32_t *w0 = words + ((y0 - fy0) * sw + (x0 - fx0));
+                    emit<CIN, OUTK>(J, o, c, w0[0], w0[1], w0[sw], w0[sw + 1], qx, qy, fx, fy);
                 }
             }
         }

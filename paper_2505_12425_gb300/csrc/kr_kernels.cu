@@ -80,9 +80,12 @@ __global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constan
 // ---------------------------------------------------------------------------
 static int round128(int x) { return (x + 127) & ~127; }
 
+// clamp: boxes larger than the caps are staged when they fit (warp); else never staged.
+// Resize boxes lie inside the image (clipped to W x H); warp boxes are not clipped.
 static Budget budget_for(int cin, double cols_d, double rows_d, int H, int W, int out_bytes, bool clamp)
 {
-    const int cols = (int)std::min<double>(cols_d, W), rows = (int)std::min<double>(rows_d, H);
+    const int cols = clamp ? (int)std::min<double>(cols_d, 1e6) : (int)std::min<double>(cols_d, W);
+    const int rows = clamp ? (int)std::min<double>(rows_d, 1e6) : (int)std::min<double>(rows_d, H);
     long long a, raw;
     if (cin == 3) {
         a = (long long)rows * word_row(cols) * 4;
