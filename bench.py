@@ -257,6 +257,40 @@ def ragged_compare(torch, kr, dev, reps=20):
     return res
 
 
+def serving_compare(torch, kr, dev, rates=(2000, 5000, 10000, 20000, 40000, 80000, 160000, 320000, 640000),
+                    seconds=1.0):
+    """Poisson request streams (sizes log-uniform 320..3840 x 240..2160, op uniform over
+    resize / warp / gray) over a device-resident pool of 64 images, 8 GB in-flight budget:
+    continuous batching (policy 0) vs one launch per request (policy 1)."""
+    sizes = inputs.pool_sizes(1004, 64)
+    pool = [torch.from_numpy(inputs.uniform_image(5000 + i, H, W, 3)).to(dev) for i, (H, W) in enumerate(sizes)]
+    arena = torch.empty(8 << 30, dtype=torch.uint8, device=dev)
+    out = {"pool_images": 64, "budget_bytes": 8 << 30, "seconds_per_rate": seconds, "streams": 4,
+           "max_batch": 64, "runs": []}
+    for rate in rates:
+        # the highest rates run for a shorter time (the stream and its host-side arrays scale with it)
+        dur = seconds if rate <= 80000 else seconds * 80000 / rate * 2
+        reqs = inputs.request_stream(1004, float(rate), dur, pool=64)
+        px = sum(r.h * r.w for r in reqs)
+        for policy in (0, 1):
+            res = kr.kr_serve_run(reqs, pool, arena, budget_bytes=8 << 30, max_batch=64, streams=4, policy=policy)
+            lat = np.array([res[i].t_done - r.t_arrival for i, r in enumerate(reqs)]) * 1e3
+            t_end = max(res[i].t_done for i in range(len(reqs)))
+            nb = len({round(res[i].t_launch, 9) for i in range(len(reqs))})
+            out["runs"].append({
+                "rate": rate, "policy": "batched" if policy == 0 else "per_image", "requests": len(reqs),
+                "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "p999_ms": round(float(np.percentile(lat, 99.9)), 3),
+                "gpx_s": round(px / t_end / 1e9, 3), "launches": nb, "mean_batch": round(len(reqs) / nb, 2)})
+    best = {}
+    for slo in (2.0, 5.0, 10.0):
+        for pol in ("batched", "per_image"):
+            ok = [r for r in out["runs"] if r["policy"] == pol and r["p99_ms"] <= slo]
+            best[f"{pol}_gpx_s_at_p99<={slo:g}ms"] = max((r["gpx_s"] for r in ok), default=None)
+    out["best"] = best
+    return out
+
+
 def cpu_baseline_sample(budget_s=12.0):
     """The oracle (single-threaded C) on a bounded sample of the step: whole frames, all eight
     operations, until the time budget is spent."""
@@ -395,6 +429,7 @@ def run_gpu(args):
            "steps": K_e2e}
 
     ragged = ragged_compare(torch, kr, dev) if not args.no_extras else None
+    serving = serving_compare(torch, kr, dev, seconds=args.serve_seconds) if not args.no_extras else None
     cpu = cpu_baseline_sample() if (rank == 0 and not args.no_extras) else None
 
     if rank == 0:
@@ -408,7 +443,7 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "no flush: 199 MB of distinct source frames per step > 129 MB L2"},
             "roofline": roofline, "per_op": breakdown, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": K * len(ops), "ragged": ragged, "clocks": clk.summary(),
+            "gpu_launches": K * len(ops), "ragged": ragged, "serving": serving, "clocks": clk.summary(),
         }
         print(json.dumps(line))
     if world > 1:
@@ -466,6 +501,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-extras", action="store_true", help="skip the ragged comparison and the CPU baseline")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="seconds of requests per serving rate")
     ap.add_argument("--images", type=int, default=inputs.BENCH_IMAGES,
                     help="frames per step (the full workload is 32; fewer only for small profiling cases)")
     args = ap.parse_args()

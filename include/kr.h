@@ -238,6 +238,74 @@ kr_status kr_autotune_save(const char *path);
 kr_status kr_autotune_load(const char *path);
 
 /* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of an open-loop request stream.             */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * One request (no counterpart in the paper: the serving form of the operators,
+ * motivated by Sec. II-B's predictable-latency goal for pre-allocated buffers).
+ * op: KR_OP_RESIZE / KR_OP_WARP / KR_OP_GRAY on source image src_index of the
+ * pool; output out_h x out_w u8 HWC with 3 channels (1 for gray, which needs the
+ * source's size); M: the warp's 2x3 destination -> source map; t_arrival:
+ * scheduled arrival in seconds from the start of the run, non-decreasing.
+ */
+typedef struct {
+    int32_t op;
+    int32_t src_index;
+    int32_t out_h, out_w;
+    float M[6];
+    double t_arrival;
+} kr_request_t;
+
+/*
+ * pool / pool_n: device-resident u8 HWC 3-channel source images (batch 1), owned
+ * by the caller; out_arena / out_arena_bytes: caller-owned DEVICE memory from
+ * which each request's output is carved (256-byte aligned, dense rows);
+ * hbm_budget_bytes: at most this many source + output bytes in flight (0 = no
+ * limit); max_batch: items per ragged launch; streams: launches in flight (the
+ * library creates and destroys these streams and their events); policy: 0 =
+ * continuous batching (kr_batch_submit on a free slot with every admitted
+ * request), 1 = one launch per request; workspaces / ws_bytes_each: policy 0
+ * only, `streams` device workspaces of ws_bytes_each >=
+ * kr_batch_workspace_size(max_batch) bytes, caller-owned; retain_outputs: 0 =
+ * a request's arena space is reused once it completes (the client is taken to
+ * consume each output at its completion), 1 = every output keeps its space until
+ * the run ends (the arena must then hold all outputs, else KR_ERR_NO_SPACE).
+ */
+typedef struct {
+    const kr_image_t *pool;
+    int32_t pool_n;
+    void *out_arena;
+    size_t out_arena_bytes;
+    size_t hbm_budget_bytes;
+    int32_t max_batch;
+    int32_t streams;
+    int32_t policy;
+    void *workspaces;
+    size_t ws_bytes_each;
+    int32_t retain_outputs;
+} kr_serve_config_t;
+
+/* Per request: admission, launch and observed completion times (seconds from the
+ * start of the run, host steady clock) and the output's byte offset in the arena. */
+typedef struct {
+    double t_admit, t_launch, t_done;
+    int64_t out_offset;
+    int32_t status;
+} kr_serve_result_t;
+
+/*
+ * Run the request stream to completion in real time on the calling thread
+ * (busy-polling). Requests wait (in arrival order) while admitting them would
+ * exceed the budget or the arena; requests that arrive while others run are
+ * admitted and launched as soon as a slot frees. Every request is validated
+ * before anything runs (KR_ERR_INVALID_ARG / KR_ERR_NO_SPACE, nothing launched).
+ * Returns when every output is complete. Results equal the single-image calls'.
+ */
+kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_serve_config_t *cfg,
+                       kr_serve_result_t *results);
+
+/* ------------------------------------------------------------------------ */
 /* Misc.                                                                    */
 /* ------------------------------------------------------------------------ */
 

@@ -58,6 +58,24 @@ class KrBatchOpts(ctypes.Structure):
     _fields_ = [("tile_config", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
 
 
+class KrRequest(ctypes.Structure):
+    _fields_ = [("op", ctypes.c_int32), ("src_index", ctypes.c_int32), ("out_h", ctypes.c_int32),
+                ("out_w", ctypes.c_int32), ("M", ctypes.c_float * 6), ("t_arrival", ctypes.c_double)]
+
+
+class KrServeConfig(ctypes.Structure):
+    _fields_ = [("pool", ctypes.POINTER(KrImage)), ("pool_n", ctypes.c_int32), ("out_arena", ctypes.c_void_p),
+                ("out_arena_bytes", ctypes.c_size_t), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32), ("policy", ctypes.c_int32),
+                ("workspaces", ctypes.c_void_p), ("ws_bytes_each", ctypes.c_size_t),
+                ("retain_outputs", ctypes.c_int32)]
+
+
+class KrServeResult(ctypes.Structure):
+    _fields_ = [("t_admit", ctypes.c_double), ("t_launch", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("out_offset", ctypes.c_int64), ("status", ctypes.c_int32)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -82,6 +100,8 @@ def load():
         lib.kr_batch_submit.argtypes = [P(KrWork), ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
                                         P(KrBatchOpts), ctypes.c_void_p]
         lib.kr_batch_submit_noalloc.argtypes = [P(KrWork), ctypes.c_int32, P(KrBatchOpts), ctypes.c_void_p]
+        lib.kr_serve_run.argtypes = [P(KrRequest), ctypes.c_int32, P(KrServeConfig), P(KrServeResult)]
+        lib.kr_device_errors.argtypes = [P(ctypes.c_uint32), ctypes.c_int32]
         lib.kr_tile_config_count.argtypes = []
         lib.kr_tile_config_count.restype = ctypes.c_int32
         lib.kr_tile_config_shape.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32)]
@@ -96,7 +116,7 @@ def load():
         lib.kr_shutdown.argtypes = []
         lib.kr_shutdown.restype = None
         for f in ("kr_resize_bilinear", "kr_warp_affine", "kr_rgb_to_gray", "kr_batch_submit",
-                  "kr_batch_submit_noalloc",
+                  "kr_batch_submit_noalloc", "kr_serve_run", "kr_device_errors",
                   "kr_tile_config_shape", "kr_autotune_batch", "kr_autotune_save", "kr_autotune_load"):
             getattr(lib, f).restype = S
         _lib = lib
@@ -288,3 +308,51 @@ def kr_status_string(status: int) -> str:
 
 def kr_shutdown():
     load().kr_shutdown()
+
+
+def kr_device_errors(clear: bool = True) -> int:
+    """Device error flags of the single-image kernels (bit 0: a TMA wait ran out)."""
+    v = ctypes.c_uint32()
+    _check(load().kr_device_errors(ctypes.byref(v), 1 if clear else 0), "kr_device_errors")
+    return v.value
+
+
+def requests_array(reqs) -> ctypes.Array:
+    """kr_request_t array from objects with op, src_index, h, w, M, t_arrival."""
+    arr = (KrRequest * len(reqs))()
+    for i, r in enumerate(reqs):
+        arr[i].op = int(r.op)
+        arr[i].src_index = int(r.src_index)
+        arr[i].out_h = int(r.h)
+        arr[i].out_w = int(r.w)
+        m = [float(v) for v in r.M.reshape(-1)]
+        for k in range(6):
+            arr[i].M[k] = m[k]
+        arr[i].t_arrival = float(r.t_arrival)
+    return arr
+
+
+def kr_serve_run(reqs, pool, arena: torch.Tensor, budget_bytes: int = 8 << 30, max_batch: int = 64,
+                 streams: int = 4, policy: int = 0, retain_outputs: bool = False):
+    """Serve `reqs` (see inputs.request_stream) over the device image `pool` (list of u8 HWC
+    tensors); outputs are carved from the device tensor `arena`. Returns the kr_serve_result_t
+    array (seconds from the start of the run; byte offsets into the arena)."""
+    lib = load()
+    arr = reqs if isinstance(reqs, ctypes.Array) else requests_array(reqs)
+    imgs = (KrImage * len(pool))()
+    for i, t in enumerate(pool):
+        imgs[i] = image(t)
+    ws = None
+    ws_each = 0
+    if policy == 0:
+        ws_each = kr_batch_workspace_size(max_batch)
+        ws_each = (ws_each + 255) // 256 * 256
+        ws = torch.empty(ws_each * streams, dtype=torch.uint8, device=arena.device)
+    cfg = KrServeConfig(imgs, len(pool), ctypes.c_void_p(arena.data_ptr()), arena.numel() * arena.element_size(),
+                        budget_bytes, max_batch, streams, policy,
+                        ctypes.c_void_p(ws.data_ptr() if ws is not None else 0), ws_each,
+                        1 if retain_outputs else 0)
+    res = (KrServeResult * len(arr))()
+    torch.cuda.synchronize()
+    _check(lib.kr_serve_run(arr, len(arr), ctypes.byref(cfg), res), "kr_serve_run")
+    return res
