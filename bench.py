@@ -60,11 +60,11 @@ def op_table():
 
 
 def kernel_source_sha() -> str:
+    """Hash of the sources of the per-operation kernels (the tile engine and its launcher)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2505_12425_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in ("kr_device.cuh", "kr_kernels.cu"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
