@@ -298,6 +298,52 @@ __device__ __forceinline__ float byte_f(uint32_t w, int k)
     return __fsub_rn(__uint_as_float(__byte_perm(w, 0x4B000000u, sel)), 8388608.f);
 }
 
+// Two fp32 lanes in one 64-bit register pair (sm_100+ packed f32x2 arithmetic).
+struct F2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ F2 f2_pack(float lo, float hi)
+{
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ F2 f2_pack_bits(uint32_t lo, uint32_t hi)
+{
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "r"(lo), "r"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(F2 a, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_sub(F2 a, F2 b)
+{
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c)
+{
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
+// R and G of a pixel word as an exact float pair (the 2^23 trick on both lanes at once).
+__device__ __forceinline__ F2 rg_f2(uint32_t w)
+{
+    const F2 biased = f2_pack_bits(__byte_perm(w, 0x4B000000u, 0x7540), __byte_perm(w, 0x4B000000u, 0x7541));
+    return f2_sub(biased, f2_pack(8388608.f, 8388608.f));
+}
+
 // Packed 11-bit weight pair for dp2a: low half 2048 - q, high half q.
 __device__ __forceinline__ uint32_t wpair(int q) { return 2048u + (uint32_t)q * 65535u; }
 
@@ -385,13 +431,23 @@ __device__ __forceinline__ void emit(const Job &J, const ORow &o, int c, uint32_
         }
     } else {
         float v[3];
-#pragma unroll
-        for (int k = 0; k < CIN; ++k) {
-            const float a = byte_f(p00, k), b = byte_f(p01, k);
-            const float cc = byte_f(p10, k), d = byte_f(p11, k);
+        if (CIN == 3) {
+            // R and G in packed f32x2 lanes, B alone: lerp along x on both rows, then along y.
+            const F2 fx2 = f2_pack(fx, fx), fy2 = f2_pack(fy, fy);
+            const F2 a = rg_f2(p00), b = rg_f2(p01), cc = rg_f2(p10), d = rg_f2(p11);
+            const F2 h0 = f2_fma(fx2, f2_sub(b, a), a);
+            const F2 h1 = f2_fma(fx2, f2_sub(d, cc), cc);
+            f2_unpack(f2_fma(fy2, f2_sub(h1, h0), h0), v[0], v[1]);
+            const float ab = byte_f(p00, 2), bb = byte_f(p01, 2), cb = byte_f(p10, 2), db = byte_f(p11, 2);
+            const float g0 = __fmaf_rn(fx, __fsub_rn(bb, ab), ab);
+            const float g1 = __fmaf_rn(fx, __fsub_rn(db, cb), cb);
+            v[2] = __fmaf_rn(fy, __fsub_rn(g1, g0), g0);
+        } else {
+            const float a = byte_f(p00, 0), b = byte_f(p01, 0);
+            const float cc = byte_f(p10, 0), d = byte_f(p11, 0);
             const float h0 = __fmaf_rn(fx, __fsub_rn(b, a), a);
             const float h1 = __fmaf_rn(fx, __fsub_rn(d, cc), cc);
-            v[k] = __fmaf_rn(fy, __fsub_rn(h1, h0), h0);
+            v[0] = __fmaf_rn(fy, __fsub_rn(h1, h0), h0);
         }
         if (OUTK == OUT_F32_GRAY) {
             const float g = __fmaf_rn(0.299f, v[0], __fmaf_rn(0.587f, v[1], __fmul_rn(0.114f, v[2])));

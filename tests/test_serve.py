@@ -147,7 +147,9 @@ def test_served_results_equal_results_alone(lib, policy):
 def test_budget_holds_and_batches_overlap(lib):
     dev = torch.device("cuda:0")
     pool = _pool(dev, n=8, seed=91, scale=0.5)
-    reqs = _stream(pool, rate=200000.0, duration=0.005, seed=9)      # a burst
+    reqs = _stream(pool, rate=200000.0, duration=0.005, seed=9)
+    for r in reqs:
+        r.t_arrival = 0.0                                             # one simultaneous burst
     nbytes = []
     for r in reqs:
         src = pool[r.src_index]
@@ -163,8 +165,9 @@ def test_budget_holds_and_batches_overlap(lib):
         cur += nbytes[i] if kind == 0 else -nbytes[i]
         peak = max(peak, cur)
     assert peak <= budget
-    # some requests had to wait for admission (the budget is tight) ...
-    assert any(res[i].t_admit - r.t_arrival > 1e-4 for i, r in enumerate(reqs))
+    # the budget admits a few requests at a time, so most of the burst waits for earlier ones ...
+    waited = sum(1 for i in range(len(reqs)) if res[i].t_admit > min(res[j].t_done for j in range(len(reqs))))
+    assert waited > len(reqs) // 2
     # ... and requests admitted while others were in flight shared batches / overlapped them
     launches = sorted({round(res[i].t_launch, 9) for i in range(len(reqs))})
     assert len(launches) < len(reqs)
