@@ -860,7 +860,9 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             }
             tma_store_commit_and_wait_read();
         }
-        __syncthreads();
+        // No closing barrier: this path runs one tile per CTA, the storing thread waits for
+        // the copy engine to finish reading the tile, and a CTA's shared memory lives until
+        // its last thread exits.
         return;
     }
 
