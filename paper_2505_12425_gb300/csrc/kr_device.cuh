@@ -688,13 +688,25 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     };
 
     if (zero_tile) {
-        // every tap lies outside the image: every output pixel is the zero sample
+        // every tap lies outside the image: every output pixel is the zero sample, which is
+        // 0 for u8 and (0 - mean[c]) / std[c] = bias[c] (bias[0] for gray) for f32
         for (int r = warp; r < ny; r += kWarps) {
             const ORow o = orow_of(r);
 #pragma unroll
             for (int j = 0; j < CPL; ++j) {
                 const int c = lane + 32 * j;
-                if (c < nx) emit<CIN, OUTK>(J, o, c, 0u, 0u, 0u, 0u, 0, 0, 0.f, 0.f);
+                if (c >= nx) continue;
+                if (!OT::is_f32) {
+#pragma unroll
+                    for (int k = 0; k < dC; ++k) o.p0[c * dC + k] = 0;
+                } else if (chw) {
+                    reinterpret_cast<float *>(o.p0)[c] = J.bias[0];
+                    reinterpret_cast<float *>(o.p1)[c] = J.bias[1];
+                    reinterpret_cast<float *>(o.p2)[c] = J.bias[2];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < dC; ++k) reinterpret_cast<float *>(o.p0)[c * dC + k] = J.bias[k];
+                }
             }
         }
     } else if (fast && CIN == 3) {
