@@ -39,6 +39,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 from paper_2505_12425_gb300 import inputs  # noqa: E402
+from paper_2505_12425_gb300.sharding import max_over_ranks  # noqa: E402
 
 METRIC = "Gpixel/s and HBM GB/s %peak for resize/warp; p50/p99 latency batched vs per-image"
 UNIT = "Gpixel/s"
@@ -367,11 +368,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-    ms_total = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(t_start.elapsed_time(t_end), dist if world > 1 else None, dev)
     ms_step = ms_total / K
     px_step = n * sum(p for _, p, _ in ops)
     value = world * px_step / (ms_step * 1e-3) / 1e9
@@ -419,11 +416,7 @@ def run_gpu(args):
             host_out[k].copy_(v, non_blocking=True)
     e1.record()
     torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1) / K_e2e
-    if world > 1:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1) / K_e2e, dist if world > 1 else None, dev)
     e2e = {"value": round(world * px_step / (ms_e2e * 1e-3) / 1e9, 3), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 3),
            "steps": K_e2e}
