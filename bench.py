@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -97,9 +98,10 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
+    def __init__(self, gpu_index: int, out_dir: str | None = None):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        out_dir = out_dir or tempfile.mkdtemp(prefix="kr_clocks_")
+        self.path = os.path.join(out_dir, f"clocks_rank{gpu_index}.csv")
         self.idx = gpu_index
 
     def __enter__(self):
@@ -357,7 +359,7 @@ def run_gpu(args):
     events = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)] for _ in ops]
               for _ in range(K)]
     t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, args.clocks_dir) as clk:
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -494,6 +496,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-extras", action="store_true", help="skip the ragged comparison and the CPU baseline")
+    ap.add_argument("--clocks-dir", default=None,
+                    help="directory for the raw nvidia-smi clock samples (default: a temporary one)")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="seconds of requests per serving rate")
     ap.add_argument("--images", type=int, default=inputs.BENCH_IMAGES,
                     help="frames per step (the full workload is 32; fewer only for small profiling cases)")
