@@ -55,9 +55,9 @@ struct Job {
     int32_t region_b;     // shared bytes of region B (raw rows of 3-channel boxes, then output tile)
     int32_t allow_fast;   // warp: the map's intermediate terms are small enough for the fast path
     // TMA (per-operation kernels; null in the ragged kernel). Both maps view images as
-    // {16 bytes, 16-byte chunk, row, (plane,) image} tensors.
-    const CUtensorMap *tin;   // source map, box {16, tin_nc, tin_br, 1}; null = cp.async staging
-    int32_t tin_nc, tin_br;
+    // {32-bit word, row, (plane,) image} tensors whose rows are a whole number of words.
+    const CUtensorMap *tin;   // source map, box {4 tin_nc words, tin_br rows, 1}; null = cp.async staging
+    int32_t tin_nc, tin_br;   // box row in 16-byte chunks, box rows
     const CUtensorMap *tout;  // destination map, box = one output tile; null = 128-bit stores
     int32_t zimg;             // image coordinate of this job in both maps
     unsigned *err;            // device error flags (bit 0: a bounded TMA wait ran out)
@@ -234,13 +234,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, uint32_t parit
     return true;
 }
 
-// 4-D tensor load {c0, c1, c2, c3} of the map's box into shared memory, completing on mbar.
-__device__ __forceinline__ void tma_load_4d(void *sdst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+// 3-D tensor load {x, y, image} of the map's box into shared memory, completing on mbar.
+__device__ __forceinline__ void tma_load_3d(void *sdst, const CUtensorMap *map, int c0, int c1, int c2,
                                             uint64_t *mbar)
 {
-    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                 " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_addr(sdst)),
-                 "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(mbar))
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                 " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_addr(sdst)),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(mbar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int c0, int c1, int c2, const void *ssrc)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(ssrc))
                  : "memory");
 }
 
@@ -249,15 +257,6 @@ __device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, int c0, int
     asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];\n" ::"l"(
                      reinterpret_cast<uint64_t>(map)),
                  "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(ssrc))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tma_store_5d(const CUtensorMap *map, int c0, int c1, int c2, int c3, int c4,
-                                             const void *ssrc)
-{
-    asm volatile("cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];\n" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(ssrc))
                  : "memory");
 }
 
@@ -572,12 +571,14 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         const int L = cols * CIN;
         const uint8_t *row0 = J.src + (int64_t)fy0 * J.spitch + (int64_t)fx0 * CIN;
         if (use_tma) {
-            // One TMA copy of the box: rows fy0.., 16-byte chunks from the one holding byte
-            // fx0*CIN of each row (rows are 16-byte aligned, so every row has the same phase).
+            // One TMA copy of the box: rows fy0.., from the 16-byte chunk holding byte fx0*CIN
+            // of each row (rows are 16-byte aligned, so every row has the same phase). Words
+            // outside the image (left of it, right of its last word, above, below) arrive as
+            // zeros: the zero border of warp boxes.
             if (tid == 0) {
                 mbar_init(&ts.mbar);
                 mbar_expect_tx(&ts.mbar, (uint32_t)(16 * J.tin_nc * J.tin_br));
-                tma_load_4d(raw, J.tin, 0, (fx0 * CIN) >> 4, fy0, J.zimg, &ts.mbar);
+                tma_load_3d(raw, J.tin, 4 * ((fx0 * CIN) >> 4), fy0, J.zimg, &ts.mbar);
                 ti.tma_ok = mbar_wait_bounded(&ts.mbar, 0, kTmaWaitNs) ? 1 : 0;
                 if (!ti.tma_ok) {
                     atomicOr(J.err, 1u);
@@ -586,17 +587,6 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             }
             __syncthreads();
             if (!ti.tma_ok) return;
-            if (OP == OP_WARP && ((J.W * CIN) & 15)) {
-                // rows end inside their last 16-byte chunk: the bytes after the last pixel
-                // are not image bytes, zero them (the copy engine filled only whole chunks)
-                const int xb0 = ((fx0 * CIN) >> 4) * 16;       // row offset of the box's first byte
-                const int z0 = J.W * CIN - xb0, z1 = ((J.W * CIN + 15) & ~15) - xb0;
-                if (z1 > 0 && z0 < 16 * J.tin_nc) {
-                    for (int r = tid; r < rows; r += kThreads)
-                        for (int b = max(z0, 0); b < min(z1, 16 * J.tin_nc); ++b) raw[r * rstride + b] = 0;
-                }
-                __syncthreads();
-            }
         } else {
         const int nchr = (L + 15 + 15) >> 4;                 // chunks a row can span
         const float inv_nchr = __frcp_rn((float)nchr);
@@ -866,9 +856,9 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         if (tid == 0) {
             if (chw) {
                 for (int pl = 0; pl < 3; ++pl)
-                    tma_store_5d(J.tout, 0, tx0 >> 2, ty0, pl, J.zimg, ostage + pl * TH * orow);
+                    tma_store_4d(J.tout, tx0, ty0, pl, J.zimg, ostage + pl * TH * orow);
             } else {
-                tma_store_4d(J.tout, 0, (tx0 * dC * ES) >> 4, ty0, J.zimg, ostage);
+                tma_store_3d(J.tout, (tx0 * dC * ES) >> 2, ty0, J.zimg, ostage);
             }
             tma_store_commit_and_wait_read();
         }

@@ -51,9 +51,10 @@ cudaError_t launch_gray(const GrayDesc &d, cudaStream_t stream);
 // Shared-memory budget of one tile: region A bytes (0 = no staging) and region B bytes
 // (at least out_bytes, the output tile). Multiples of 16.
 struct Budget {
-    int a;
-    int b;
-    int cols, rows;   // bound of a tile's source box (pixels), clipped to the image
+    int a = 0;
+    int b = 0;
+    int cols = 0, rows = 0;   // bound of a tile's source box (pixels), clipped to the image
+    bool fits = false;        // a box of that bound fits the staging caps
 };
 Budget budget_resize(int cin, int H, int W, int h, int w, int tw, int th, int out_bytes);
 Budget budget_warp(int cin, int H, int W, const float *M, int tw, int th, int out_bytes);

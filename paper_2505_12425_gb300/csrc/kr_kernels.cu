@@ -98,6 +98,7 @@ static Budget budget_for(int cin, double cols_d, double rows_d, int H, int W, in
     b.cols = cols;
     b.rows = rows;
     if (a <= kFootCap && raw <= kRegionBCap) {
+        b.fits = true;
         b.a = round128((int)a);
         b.b = round16((int)std::max<long long>(out_bytes, raw));
     } else if (clamp) {
@@ -141,7 +142,7 @@ bool warp_allows_fast(const float *M, int h, int w)
 }
 
 // ---------------------------------------------------------------------------
-// TMA tensor maps: images as {16 bytes, 16-byte chunk, row, (plane,) image} tensors
+// TMA tensor maps: images as {32-bit word, row, (plane,) image} tensors
 // ---------------------------------------------------------------------------
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
@@ -158,17 +159,19 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// Map over n images of `rows` rows whose first `rowbytes` bytes are used, with an extra
-// plane dimension when planes > 1. Box: {16, box_chunks, box_rows, 1(, 1)}. Returns false
-// (and the caller keeps the non-TMA path) when the layout does not meet TMA's rules.
+// Map over n images of `rows` rows of `rowbytes` bytes, with an extra plane dimension when
+// planes > 1. Elements are 32-bit words, so a row must be a whole number of words (the map
+// then never reads past a row's own bytes). Box: {box_chunks 16-byte chunks, box_rows, 1(, 1)}.
+// Returns false (and the caller keeps the non-TMA path) when the layout does not meet TMA's rules.
 static bool encode_map(CUtensorMap *m, const void *base, int64_t rowbytes, int rows, int planes, int n,
                        int64_t pitch, int64_t pstride, int64_t bstride, int box_chunks, int box_rows)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
-    const int64_t nchunk = (rowbytes + 15) / 16;
-    if (((uintptr_t)base & 15) || (pitch & 15) || pitch < nchunk * 16) return false;
-    if (box_chunks < 1 || box_chunks > 256 || box_rows < 1 || box_rows > 256) return false;
+    if ((rowbytes & 3) || rowbytes < 4) return false;
+    if (((uintptr_t)base & 15) || (pitch & 15) || pitch < rowbytes) return false;
+    // the box's first dimension is at most 256 elements
+    if (box_chunks < 1 || box_chunks > 64 || box_rows < 1 || box_rows > 256) return false;
     const int64_t pe = planes > 1 ? pstride : (int64_t)rows * pitch;          // plane extent
     const int64_t be = n > 1 ? bstride : (planes > 1 ? planes * pstride : (int64_t)rows * pitch);
     if (planes > 1 && ((pe & 15) || pe < (int64_t)rows * pitch)) return false;
@@ -177,14 +180,13 @@ static bool encode_map(CUtensorMap *m, const void *base, int64_t rowbytes, int r
     cuuint64_t strides[4];
     cuuint32_t box[5], es[5] = {1, 1, 1, 1, 1};
     int rank = 0;
-    dims[rank] = 16; box[rank] = 16; ++rank;
-    dims[rank] = (cuuint64_t)nchunk; box[rank] = (cuuint32_t)box_chunks; strides[rank - 1] = 16; ++rank;
+    dims[rank] = (cuuint64_t)(rowbytes / 4); box[rank] = (cuuint32_t)(4 * box_chunks); ++rank;
     dims[rank] = (cuuint64_t)rows; box[rank] = (cuuint32_t)box_rows; strides[rank - 1] = (cuuint64_t)pitch; ++rank;
     if (planes > 1) {
         dims[rank] = (cuuint64_t)planes; box[rank] = 1; strides[rank - 1] = (cuuint64_t)pe; ++rank;
     }
     dims[rank] = (cuuint64_t)n; box[rank] = 1; strides[rank - 1] = (cuuint64_t)((be + 15) & ~(int64_t)15); ++rank;
-    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, rank, const_cast<void *>(base), dims, strides, box, es,
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, rank, const_cast<void *>(base), dims, strides, box, es,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -242,6 +244,10 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
                 const Budget bi = budget_warp(CIN, d.H, d.W, p.M[i], TW, TH, ob);
                 bud.a = std::max(bud.a, bi.a);
                 bud.b = std::max(bud.b, bi.b);
+                if (bi.fits) {   // the TMA box covers every image whose tiles' boxes fit the caps
+                    bud.cols = std::max(bud.cols, bi.cols);
+                    bud.rows = std::max(bud.rows, bi.rows);
+                }
                 if (warp_allows_fast(p.M[i], d.h, d.w)) p.fast_mask[i >> 5] |= 1u << (i & 31);
             }
         }
@@ -251,7 +257,7 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
         p.dst = d.dst + (int64_t)b0 * d.dbatch;
         // TMA source map: one box per tile covering the largest source box of the launch
         p.has_tin = 0;
-        if (bud.a > 0) {
+        if (bud.a > 0 && bud.cols > 0 && bud.rows > 0) {
             const int nc = (15 + bud.cols * CIN + 15) / 16, br = bud.rows;
             const long long cap = CIN == 3 ? bud.b : bud.a - 16;
             if ((long long)16 * nc * br <= cap &&

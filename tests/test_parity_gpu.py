@@ -194,9 +194,9 @@ def _special_matrices(H, W):
     }
 
 
+@pytest.mark.parametrize("H,W", [(67, 93), (64, 96)])     # 96 * 3 bytes per row: TMA staging
 @pytest.mark.parametrize("name", list(_special_matrices(1, 1)))
-def test_warp_special_matrices(name):
-    H, W = 67, 93
+def test_warp_special_matrices(name, H, W):
     img = inputs.uniform_image(21, H, W, 3)
     M = np.array(_special_matrices(H, W)[name], np.float32)
     out = Guarded((H, W, 3), torch.uint8)
@@ -253,6 +253,36 @@ def test_views_with_odd_pitch_and_offset():
         m = torch.ones(b.shape[:2], dtype=torch.bool, device=dev())
         m[sl] = False
         assert bool((b[m] == CANARY_U8).all()), "write outside the destination view"
+
+
+def test_tma_staging_of_padded_views():
+    # Rows of 100 pixels (300 bytes, a whole number of words) inside rows of 112 (336
+    # bytes, a multiple of 16) that start 16-byte aligned: the source is staged by TMA. The
+    # row padding (set to 200 here) must never be read: right of each row the copy engine
+    # fills zeros, the zero border of warp boxes.
+    n, H, Wp, W = 3, 150, 112, 100
+    imgs = np.stack([inputs.noise_gradient_image(60 + i, H, W) for i in range(n)])
+    big = torch.full((n, H, Wp, 3), 200, dtype=torch.uint8, device=dev())
+    big[:, :, :W] = to_dev(imgs)
+    src = big[:, :, :W]
+    Ms = inputs.warp_matrices(60, n, H, W)
+    wu = Guarded((n, H, W, 3), torch.uint8)
+    kr.kr_warp_affine(src, wu.t, Ms)
+    wf = Guarded((n, 3, H, W), torch.float32)
+    kr.kr_warp_affine(src, wf.t, Ms, mean=MEAN, std=STD, dst_layout="chw")
+    wg = Guarded((n, H, W, 1), torch.uint8)
+    kr.kr_warp_affine(src, wg.t, Ms, gray=True)
+    r = Guarded((n, 77, 190, 3), torch.uint8)
+    kr.kr_resize_bilinear(src, r.t)
+    torch.cuda.synchronize()
+    for g in (wu, wf, wg, r):
+        g.check()
+    for i in range(n):
+        np.testing.assert_array_equal(wu.np()[i], oracle.warp_u8(imgs[i], Ms[i], H, W))
+        np.testing.assert_array_equal(wg.np()[i], oracle.warp_u8(imgs[i], Ms[i], H, W, gray=True))
+        ref = oracle.warp_f64(imgs[i], Ms[i], H, W, mean=MEAN, std=STD)
+        assert np.abs(wf.np()[i].transpose(1, 2, 0) - ref).max() <= F32_TOL
+        np.testing.assert_array_equal(r.np()[i], oracle.resize_u8(imgs[i], 77, 190))
 
 
 def test_batch_dimension_one_call():
