@@ -94,6 +94,7 @@ __device__ __forceinline__ Job job_of(const WorkItem &it)
     J.allow_fast = it.allow_fast;
     J.tin = nullptr;
     J.tin_nc = J.tin_br = 0;
+    J.raw_taps = 0;
     J.tout = nullptr;
     J.zimg = 0;
     J.err = nullptr;

@@ -54,6 +54,8 @@ struct Job {
     int32_t foot_budget;  // shared bytes of region A (staged box); 0 = never stage
     int32_t region_b;     // shared bytes of region B (raw rows of 3-channel boxes, then output tile)
     int32_t allow_fast;   // warp: the map's intermediate terms are small enough for the fast path
+    int32_t raw_taps;     // 3-channel tiles staged by TMA read their taps from the raw rows in
+                          // region A (sized for the source map's box) instead of re-laying them
     // TMA (per-operation kernels; null in the ragged kernel). Both maps view images as
     // {32-bit word, row, (plane,) image} tensors whose rows are a whole number of words.
     const CUtensorMap *tin;   // source map, box {4 tin_nc words, tin_br rows, 1}; null = cp.async staging
@@ -401,11 +403,55 @@ struct ORow {
     uint8_t *p0, *p1, *p2;
 };
 
+// Tap formats of a 3-channel pixel pair (x0, x0 + 1) of one source row:
+//   TAPS_WORDS  p0 = R0 | G0<<8 | B0<<16, p1 = R1 | G1<<8 | B1<<16 (re-laid box);
+//   TAPS_RAW    p0 = R0 | G0<<8 | B0<<16 | R1<<24, p1 = G1 | B1<<8 | .. (the six bytes
+//               of the pair as they lie in a raw row, shifted down to byte 0).
+enum { TAPS_WORDS = 0, TAPS_RAW = 1 };
+template <int V> struct IntC {
+    static constexpr int value = V;
+};
+
+// Raw pair at byte offset `off` of a staged box: three aligned words, two funnel shifts
+// (which use the low five bits of the shift, so off * 8 needs no mask).
+__device__ __forceinline__ void raw_pair(const uint8_t *wp, uint32_t sh, uint32_t &p0, uint32_t &p1)
+{
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(wp);
+    const uint32_t t0 = w[0], t1 = w[1], t2 = w[2];
+    p0 = __funnelshift_r(t0, t1, sh);
+    p1 = __funnelshift_r(t1, t2, sh);
+}
+
+// Horizontal u8 blend of the pair (p0, p1) in tap format F with weight pair w.
+template <int F>
+__device__ __forceinline__ U8x3 hblend_pair(uint32_t p0, uint32_t p1, uint32_t w)
+{
+    if (F == TAPS_WORDS) return hblend_px(p0, p1, w);
+    const uint32_t rg = __byte_perm(p0, p1, 0x4130);   // R0 R1 G0 G1
+    const uint32_t bb = __byte_perm(p0, p1, 0x0052);   // B0 B1
+    U8x3 o;
+    o.r = __dp2a_lo(w, rg, 0u);
+    o.g = __dp2a_hi(w, rg, 0u);
+    o.b = __dp2a_lo(w, bb, 0u);
+    return o;
+}
+
+// R, G of the pair's second pixel as an exact float pair, and B of both pixels.
+template <int F>
+__device__ __forceinline__ F2 rg1_f2(uint32_t p0, uint32_t p1)
+{
+    if (F == TAPS_WORDS) return rg_f2(p1);
+    const F2 biased = f2_pack_bits(__byte_perm(p0, 0x4B000000u, 0x7543), __byte_perm(p1, 0x4B000000u, 0x7540));
+    return f2_sub(biased, f2_pack(8388608.f, 8388608.f));
+}
+template <int F> __device__ __forceinline__ float b1_f(uint32_t p1) { return byte_f(p1, F == TAPS_WORDS ? 2 : 1); }
+
 // ---------------------------------------------------------------------------
 // Per-pixel output: blend the taps and put the result into the output tile.
-// Taps are words R | G<<8 | B<<16 (3 channels) or the pixel in byte 0 (1 channel).
+// Taps are pixel pairs (p00, p01) of the top row and (p10, p11) of the bottom row in
+// tap format F (3 channels), or single pixels in byte 0 (1 channel).
 // ---------------------------------------------------------------------------
-template <int CIN, int OUTK>
+template <int CIN, int OUTK, int F = TAPS_WORDS>
 __device__ __forceinline__ void emit(const Job &J, const ORow &o, int c, uint32_t p00, uint32_t p01,
                                      uint32_t p10, uint32_t p11, int qx, int qy, float fx, float fy)
 {
@@ -414,7 +460,7 @@ __device__ __forceinline__ void emit(const Job &J, const ORow &o, int c, uint32_
         uint8_t *op = o.p0 + c * OT::dC;
         const uint32_t w = wpair(qx);
         if (CIN == 3) {
-            const U8x3 a = hblend_px(p00, p01, w), b = hblend_px(p10, p11, w);
+            const U8x3 a = hblend_pair<F>(p00, p01, w), b = hblend_pair<F>(p10, p11, w);
             const uint32_t r = vblend(a.r, b.r, qy), g = vblend(a.g, b.g, qy), bl = vblend(a.b, b.b, qy);
             if (OUTK == OUT_U8_GRAY) {
                 op[0] = (uint8_t)gray_u8(r, g, bl);
@@ -433,11 +479,11 @@ __device__ __forceinline__ void emit(const Job &J, const ORow &o, int c, uint32_
         if (CIN == 3) {
             // R and G in packed f32x2 lanes, B alone: lerp along x on both rows, then along y.
             const F2 fx2 = f2_pack(fx, fx), fy2 = f2_pack(fy, fy);
-            const F2 a = rg_f2(p00), b = rg_f2(p01), cc = rg_f2(p10), d = rg_f2(p11);
+            const F2 a = rg_f2(p00), b = rg1_f2<F>(p00, p01), cc = rg_f2(p10), d = rg1_f2<F>(p10, p11);
             const F2 h0 = f2_fma(fx2, f2_sub(b, a), a);
             const F2 h1 = f2_fma(fx2, f2_sub(d, cc), cc);
             f2_unpack(f2_fma(fy2, f2_sub(h1, h0), h0), v[0], v[1]);
-            const float ab = byte_f(p00, 2), bb = byte_f(p01, 2), cb = byte_f(p10, 2), db = byte_f(p11, 2);
+            const float ab = byte_f(p00, 2), bb = b1_f<F>(p01), cb = byte_f(p10, 2), db = b1_f<F>(p11);
             const float g0 = __fmaf_rn(fx, __fsub_rn(bb, ab), ab);
             const float g1 = __fmaf_rn(fx, __fsub_rn(db, cb), cb);
             v[2] = __fmaf_rn(fy, __fsub_rn(g1, g0), g0);
@@ -543,20 +589,24 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     const int srow = raw_row_bytes(max(cols, 1), CIN), sw = word_row(max(cols, 1));
     const bool zero_tile = OP == OP_WARP && ti.zero != 0;
     bool staged = !zero_tile && cols >= 1 && rows >= 1 && J.foot_budget > 0;
-    if (staged) {
+    // TMA staging when the launch has a source map whose box holds this tile's box.
+    const bool tma_fits = staged && J.tin != nullptr && rows <= J.tin_br &&
+                          ((fx0 * CIN) & 15) + cols * CIN <= 16 * J.tin_nc;
+    // Raw taps: 3-channel taps are read straight from the TMA-staged rows (region A, which
+    // the launch sized for the map's box), whose 16-byte phase is the same for every row.
+    const bool rawbox = CIN == 3 && J.raw_taps && tma_fits;
+    if (staged && !rawbox) {
         if (CIN == 3)
             staged = (long long)rows * sw * 4 <= J.foot_budget && (long long)rows * srow <= J.region_b;
         else
             staged = (long long)rows * srow + 16 <= J.foot_budget;
     }
     const bool fast = staged && (OP == OP_RESIZE || ti.fast != 0);   // resize taps always lie in the box
-    // TMA staging when the launch has a source map whose box holds this tile's box.
-    const bool use_tma = staged && J.tin != nullptr && rows <= J.tin_br &&
-                         ((fx0 * CIN) & 15) + cols * CIN <= 16 * J.tin_nc;
+    const bool use_tma = staged && tma_fits;
     const int rstride = use_tma ? 16 * J.tin_nc : srow;   // bytes between staged raw rows
     uint8_t *regA = smem;
     uint8_t *regB = smem + J.foot_budget;
-    uint8_t *raw = CIN == 3 ? regB : regA;
+    uint8_t *raw = (CIN == 3 && !rawbox) ? regB : regA;
     uint8_t *ostage = regB;
     const uint32_t *words = reinterpret_cast<const uint32_t *>(regA);
 
@@ -627,7 +677,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         cp_async_wait_all();
         __syncthreads();
         }
-        if (CIN == 3) {
+        if (CIN == 3 && !rawbox) {
             // Re-lay each row as one word per pixel, 4 pixels (12 bytes) per step.
             const int gpr = (cols + 3) >> 2;
             const float inv_gpr = __frcp_rn((float)gpr);
@@ -658,6 +708,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     const bool chw = OT::is_f32 && dC == 3 && J.chw;
     // output rows: dense when the tile leaves through a TMA store (its rows are 16-byte
     // aligned), else with room for each row's 16-byte phase
+    const int rph = (fx0 * CIN) & 15;   // phase of every TMA-staged row (raw taps)
     const bool tma_out = J.tout != nullptr;
     const int orow = tma_out ? (chw ? TW * 4 : TW * dC * ES) : (chw ? round16(TW * 4 + 15) : round16(TW * dC * ES + 15));
     // low address bits of output row 0 of the tile (plane 0): staging rows keep their phase
@@ -700,37 +751,110 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             }
         }
     } else if (fast && CIN == 3) {
-        const int wbase = -(fy0 * sw + fx0);
-        if (OP == OP_RESIZE) {
-            int xo[CPL], xo1[CPL], qxs[CPL];   // word offsets of the two column taps in a box row
-            float fxs[CPL];
-#pragma unroll
-            for (int j = 0; j < CPL; ++j) {
-                const int c = lane + 32 * j;
-                xo[j] = ts.cx0[c] - fx0;
-                xo1[j] = xo[j] + (ts.cqd[c] >> 16);
-                qxs[j] = ts.cqd[c] & 0xFFFF;
-                fxs[j] = ts.cf[c];
-            }
-            for (int r = warp; r < ny; r += kWarps) {
-                const int y0 = ts.ry0[r], qy = ts.rqd[r] & 0xFFFF, dy = ts.rqd[r] >> 16;
-                const float fy = ts.rf[r];
-                const uint32_t *w0 = words + (y0 - fy0) * sw;
-                const uint32_t *w1 = w0 + dy * sw;
-                const ORow o = orow_of(r);
+        // Taps are addressed box-relative: word index into the re-laid box (TAPS_WORDS) or
+        // byte offset into the raw rows, every row starting at phase rph (TAPS_RAW).
+        auto fast3 = [&](auto fmt) {
+            constexpr int F = decltype(fmt)::value;
+            if (OP == OP_RESIZE) {
+                int xo[CPL], xo1[CPL], qxs[CPL];   // left tap (word index / byte offset), right tap
+                float fxs[CPL];
 #pragma unroll
                 for (int j = 0; j < CPL; ++j) {
                     const int c = lane + 32 * j;
-                    if (c < nx)
-                        emit<CIN, OUTK>(J, o, c, w0[xo[j]], w0[xo1[j]], w1[xo[j]], w1[xo1[j]], qxs[j], qy,
-                                        fxs[j], fy);
+                    const int xr = ts.cx0[c] - fx0;
+                    xo[j] = F == TAPS_RAW ? rph + 3 * xr : xr;
+                    xo1[j] = xr + (ts.cqd[c] >> 16);
+                    qxs[j] = ts.cqd[c] & 0xFFFF;
+                    fxs[j] = ts.cf[c];
+                }
+                for (int r = warp; r < ny; r += kWarps) {
+                    const int y0 = ts.ry0[r], qy = ts.rqd[r] & 0xFFFF, dy = ts.rqd[r] >> 16;
+                    const float fy = ts.rf[r];
+                    const ORow o = orow_of(r);
+                    if (F == TAPS_RAW) {
+                        // the pair (x0, x0 + 1) even where x1 = x0 (right edge): there q = 0
+                        const uint8_t *b0 = raw + (y0 - fy0) * rstride;
+                        const int d1 = dy * rstride;
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j) {
+                            const int c = lane + 32 * j;
+                            if (c < nx) {
+                                uint32_t p00, p01, p10, p11;
+                                const uint8_t *wp = b0 + (xo[j] & ~3);
+                                const uint32_t sh = (uint32_t)xo[j] << 3;
+                                raw_pair(wp, sh, p00, p01);
+                                raw_pair(wp + d1, sh, p10, p11);
+                                emit<CIN, OUTK, F>(J, o, c, p00, p01, p10, p11, qxs[j], qy, fxs[j], fy);
+                            }
+                        }
+                    } else {
+                        const uint32_t *w0 = words + (y0 - fy0) * sw;
+                        const uint32_t *w1 = w0 + dy * sw;
+#pragma unroll
+                        for (int j = 0; j < CPL; ++j) {
+                            const int c = lane + 32 * j;
+                            if (c < nx)
+                                emit<CIN, OUTK>(J, o, c, w0[xo[j]], w0[xo1[j]], w1[xo[j]], w1[xo1[j]], qxs[j], qy,
+                                                fxs[j], fy);
+                        }
+                    }
+                }
+            } else {
+                // warp: per pixel a = m00 (x + 1/2) + row term (fp32 fma), then the fast weight form
+                float xcs[CPL];
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) xcs[j] = __fadd_rn((float)(tx0 + lane + 32 * j), 0.5f);
+                // top-left tap from the source coordinates: word index y0 sw + x0 + abase, or
+                // byte offset y0 rstride + 3 x0 + abase
+                const int abase = F == TAPS_RAW ? rph - fy0 * rstride - 3 * fx0 : -(fy0 * sw + fx0);
+                for (int r = warp; r < ny; r += kWarps) {
+                    const float yc = __fadd_rn((float)(ty0 + r), 0.5f);
+                    const float rx = __fmaf_rn(J.M[1], yc, J.M[2]);
+                    const float ry = __fmaf_rn(J.M[4], yc, J.M[5]);
+                    const ORow o = orow_of(r);
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j) {
+                        const int c = lane + 32 * j;
+                        if (c < nx) {
+                            const float ax = __fmaf_rn(J.M[0], xcs[j], rx);
+                            const float ay = __fmaf_rn(J.M[3], xcs[j], ry);
+                            int x0, y0, qx = 0, qy = 0;
+                            float fx = 0.f, fy = 0.f;
+                            if (!OT::is_f32) {
+                                const int Tx = warp_fixed_fast(ax), Ty = warp_fixed_fast(ay);
+                                x0 = Tx >> 11; qx = Tx & 2047;
+                                y0 = Ty >> 11; qy = Ty & 2047;
+                            } else {
+                                const float sx = __fsub_rn(ax, 0.5f), sy = __fsub_rn(ay, 0.5f);
+                                x0 = __float2int_rd(sx);
+                                y0 = __float2int_rd(sy);
+                                // exact float of x0 in [0, 2^23): 2^23 + x0 has x0 in its mantissa
+                                fx = __fsub_rn(sx, __fsub_rn(__int_as_float(0x4B000000 + x0), 8388608.f));
+                                fy = __fsub_rn(sy, __fsub_rn(__int_as_float(0x4B000000 + y0), 8388608.f));
+                            }
+                            if (F == TAPS_RAW) {
+                                const int off = y0 * rstride + 3 * x0 + abase;
+                                const uint8_t *wp = raw + (off & ~3);
+                                const uint32_t sh = (uint32_t)off << 3;
+                                uint32_t p00, p01, p10, p11;
+                                raw_pair(wp, sh, p00, p01);
+                                raw_pair(wp + rstride, sh, p10, p11);
+                                emit<CIN, OUTK, F>(J, o, c, p00, p01, p10, p11, qx, qy, fx, fy);
+                            } else {
+                                const uint32_t *w0 = words + (y0 * sw + x0 + abase);
+                                emit<CIN, OUTK>(J, o, c, w0[0], w0[1], w0[sw], w0[sw + 1], qx, qy, fx, fy);
+                            }
+                        }
+                    }
                 }
             }
-        } else {
-            // warp: per pixel a = m00 (x + 1/2) + row term (fp32 fma), then the fast weight form
-            float xcs[CPL];
-#pragma unroll
-            for (int j = 0; j < CPL; ++j) xcs[j] = __fadd_rn((float)(tx0 + lane + 32 * j), 0.5f);
+        };
+        if (rawbox) fast3(IntC<TAPS_RAW>{}); else fast3(IntC<TAPS_WORDS>{});
+    } else if (OP == OP_WARP && CIN == 3 && staged) {
+        // Medium path (warp tiles with coordinates outside [0, 4094)): the exact weight
+        // formula per pixel; every tap still lies in the zero-filled box.
+        auto medium3 = [&](auto fmt) {
+            constexpr int F = decltype(fmt)::value;
             for (int r = warp; r < ny; r += kWarps) {
                 const float yc = __fadd_rn((float)(ty0 + r), 0.5f);
                 const float rx = __fmaf_rn(J.M[1], yc, J.M[2]);
@@ -740,56 +864,34 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                 for (int j = 0; j < CPL; ++j) {
                     const int c = lane + 32 * j;
                     if (c < nx) {
-                        const float ax = __fmaf_rn(J.M[0], xcs[j], rx);
-                        const float ay = __fmaf_rn(J.M[3], xcs[j], ry);
-                        int x0, y0, qx = 0, qy = 0;
+                        const float xc = __fadd_rn((float)(tx0 + c), 0.5f);
+                        const float sx = __fsub_rn(__fmaf_rn(J.M[0], xc, rx), 0.5f);
+                        const float sy = __fsub_rn(__fmaf_rn(J.M[3], xc, ry), 0.5f);
+                        int x0, y0, qx, qy;
+                        warp_weight(sx, x0, qx);
+                        warp_weight(sy, y0, qy);
                         float fx = 0.f, fy = 0.f;
-                        if (!OT::is_f32) {
-                            const int Tx = warp_fixed_fast(ax), Ty = warp_fixed_fast(ay);
-                            x0 = Tx >> 11; qx = Tx & 2047;
-                            y0 = Ty >> 11; qy = Ty & 2047;
-                        } else {
-                            const float sx = __fsub_rn(ax, 0.5f), sy = __fsub_rn(ay, 0.5f);
-                            x0 = __float2int_rd(sx);
-                            y0 = __float2int_rd(sy);
-                            // exact float of x0 in [0, 2^23): 2^23 + x0 has x0 in its mantissa
-                            fx = __fsub_rn(sx, __fsub_rn(__int_as_float(0x4B000000 + x0), 8388608.f));
-                            fy = __fsub_rn(sy, __fsub_rn(__int_as_float(0x4B000000 + y0), 8388608.f));
+                        if (OT::is_f32) {
+                            fx = __fsub_rn(sx, floorf(sx));
+                            fy = __fsub_rn(sy, floorf(sy));
                         }
-                        const uint32_t *w0 = words + (y0 * sw + x0 + wbase);
-                        emit<CIN, OUTK>(J, o, c, w0[0], w0[1], w0[sw], w0[sw + 1], qx, qy, fx, fy);
+                        if (F == TAPS_RAW) {
+                            const int off = (y0 - fy0) * rstride + 3 * (x0 - fx0) + rph;
+                            const uint8_t *wp = raw + (off & ~3);
+                            const uint32_t sh = (uint32_t)off << 3;
+                            uint32_t p00, p01, p10, p11;
+                            raw_pair(wp, sh, p00, p01);
+                            raw_pair(wp + rstride, sh, p10, p11);
+                            emit<CIN, OUTK, F>(J, o, c, p00, p01, p10, p11, qx, qy, fx, fy);
+                        } else {
+                            const uint32_t *w0 = words + ((y0 - fy0) * sw + (x0 - fx0));
+                            emit<CIN, OUTK>(J, o, c, w0[0], w0[1], w0[sw], w0[sw + 1], qx, qy, fx, fy);
+                        }
                     }
                 }
             }
-        }
-    } else if (OP == OP_WARP && CIN == 3 && staged) {
-        // Medium path (warp tiles with coordinates outside [0, 4094)): the exact weight
-        // formula per pixel; every tap still lies in the zero-filled box.
-        for (int r = warp; r < ny; r += kWarps) {
-            const float yc = __fadd_rn((float)(ty0 + r), 0.5f);
-            const float rx = __fmaf_rn(J.M[1], yc, J.M[2]);
-            const float ry = __fmaf_rn(J.M[4], yc, J.M[5]);
-            const ORow o = orow_of(r);
-#pragma unroll
-            for (int j = 0; j < CPL; ++j) {
-                const int c = lane + 32 * j;
-                if (c < nx) {
-                    const float xc = __fadd_rn((float)(tx0 + c), 0.5f);
-                    const float sx = __fsub_rn(__fmaf_rn(J.M[0], xc, rx), 0.5f);
-                    const float sy = __fsub_rn(__fmaf_rn(J.M[3], xc, ry), 0.5f);
-                    int x0, y0, qx, qy;
-                    warp_weight(sx, x0, qx);
-                    warp_weight(sy, y0, qy);
-                    float fx = 0.f, fy = 0.f;
-                    if (OT::is_f32) {
-                        fx = __fsub_rn(sx, floorf(sx));
-                        fy = __fsub_rn(sy, floorf(sy));
-                    }
-                    const uint32_t *w0 = words + ((y0 - fy0) * sw + (x0 - fx0));
-                    emit<CIN, OUTK>(J, o, c, w0[0], w0[1], w0[sw], w0[sw + 1], qx, qy, fx, fy);
-                }
-            }
-        }
+        };
+        if (rawbox) medium3(IntC<TAPS_RAW>{}); else medium3(IntC<TAPS_WORDS>{});
     } else {
         // General path: per-pixel coordinates with the full rules; taps from the
         // staged box when inside it, else from global memory (zero outside the image).
@@ -820,6 +922,8 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                 uint32_t p00 = 0, p01 = 0, p10 = 0, p11 = 0;
                 if (valid) {
                     const bool in_box = staged && x0 >= fx0 && x0 + dx <= fx1 && y0 >= fy0 && y0 + dy <= fy1;
+                    // (3-channel tiles get here only unstaged: staged ones take the fast or
+                    // medium path)
                     if (in_box && CIN == 3) {
                         const uint32_t *w0 = words + ((y0 - fy0) * sw + (x0 - fx0));
                         const uint32_t *w1 = w0 + dy * sw;

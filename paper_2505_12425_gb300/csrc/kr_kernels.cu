@@ -34,6 +34,7 @@ struct OpParams {
     int32_t chw;
     int32_t foot_budget;
     int32_t region_b;
+    int32_t raw_taps;
     uint32_t fast_mask[(kMaxMPerLaunch + 31) / 32];   // warp: images whose map allows the fast path
     float scale[3], bias[3];
     float M[kMaxMPerLaunch][6];
@@ -58,6 +59,7 @@ __global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constan
     J.chw = p.chw;
     J.foot_budget = p.foot_budget;
     J.region_b = p.region_b;
+    J.raw_taps = p.raw_taps;
     J.allow_fast = OP == OP_WARP ? (int)((p.fast_mask[z >> 5] >> (z & 31)) & 1u) : 1;
     J.tin = p.has_tin ? &p.tin : nullptr;
     J.tin_nc = p.tin_nc;
@@ -251,12 +253,11 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
                 if (warp_allows_fast(p.M[i], d.h, d.w)) p.fast_mask[i >> 5] |= 1u << (i & 31);
             }
         }
-        p.foot_budget = bud.a;
-        p.region_b = bud.b;
         p.src = d.src + (int64_t)b0 * d.sbatch;
         p.dst = d.dst + (int64_t)b0 * d.dbatch;
         // TMA source map: one box per tile covering the largest source box of the launch
         p.has_tin = 0;
+        p.raw_taps = 0;
         if (bud.a > 0 && bud.cols > 0 && bud.rows > 0) {
             const int nc = (15 + bud.cols * CIN + 15) / 16, br = bud.rows;
             const long long cap = CIN == 3 ? bud.b : bud.a - 16;
@@ -265,8 +266,18 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
                 p.has_tin = 1;
                 p.tin_nc = nc;
                 p.tin_br = br;
+                if (CIN == 3) {
+                    // 3-channel taps straight from the staged rows: region A holds the map's
+                    // box plus the 16 bytes that reading the last pixel pair may touch past
+                    // it, region B only the output tile
+                    p.raw_taps = 1;
+                    bud.a = round128(16 * nc * br + 16);
+                    bud.b = round16(ob);
+                }
             }
         }
+        p.foot_budget = bud.a;
+        p.region_b = bud.b;
         // TMA destination map: whole tiles, when every row is a whole number of 16-byte chunks
         p.has_tout = 0;
         constexpr int dC = OutTraits<OUTK, CIN>::dC, ES = OutTraits<OUTK, CIN>::esize;
