@@ -166,14 +166,6 @@ __device__ __forceinline__ void warp_weight(float s, int &i0, int &q)
     q = (int)k + (__fsub_rn(t, k) >= 0.5f ? 1 : 0);
 }
 
-// Fast form of warp_weight for a = s + 1/2 with s in [0, 4094): T = floor(2048 a - 1023.5)
-// computed with one rounding equals 2048 * floor(s) + q exactly (every fp32 value of the
-// range is checked on the host). q = 2048 comes out as (floor(s) + 1, 0): the same sample.
-__device__ __forceinline__ int warp_fixed_fast(float a)
-{
-    return __float2int_rd(__fmaf_rn(a, 2048.f, -1023.5f));
-}
-
 // ---------------------------------------------------------------------------
 // Small helpers
 // ---------------------------------------------------------------------------
@@ -335,6 +327,24 @@ __device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c)
 {
     F2 r;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
+__device__ __forceinline__ void f2_unpack_bits(F2 a, uint32_t &lo, uint32_t &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(lo), "=r"(hi) : "l"(a.v));
+}
+// Rounded toward minus infinity, lane by lane.
+__device__ __forceinline__ F2 f2_fma_rm(F2 a, F2 b, F2 c)
+{
+    F2 r;
+    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_add_rm(F2 a, F2 b)
+{
+    F2 r;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
     return r;
 }
 
@@ -800,40 +810,52 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                     }
                 }
             } else {
-                // warp: per pixel a = m00 (x + 1/2) + row term (fp32 fma), then the fast weight form
-                float xcs[CPL];
+                // warp: (ax, ay) = (m00, m10) (x + 1/2) + row terms, the two axes in one packed
+                // lane pair (fp32 fmas, lane by lane as in the definition), then the fast forms,
+                // both rounded toward minus infinity (exact on [0, 4094), checked exhaustively
+                // on the host):
+                //   u8   fma(a, 2048, 2^23 - 1023.5) = 2^23 + 2048 x0 + q  (bits 0x4B000000 + ..;
+                //        q = 2048 comes out as x0 + 1 with q = 0, the same sample)
+                //   f32  a + (2^23 - 1/2) = 2^23 + x0; the weight of x0 + 1 is a - (x0 + 1/2)
+                F2 xc2[CPL];
 #pragma unroll
-                for (int j = 0; j < CPL; ++j) xcs[j] = __fadd_rn((float)(tx0 + lane + 32 * j), 0.5f);
-                // top-left tap from the source coordinates: word index y0 sw + x0 + abase, or
-                // byte offset y0 rstride + 3 x0 + abase
-                const int abase = F == TAPS_RAW ? rph - fy0 * rstride - 3 * fx0 : -(fy0 * sw + fx0);
+                for (int j = 0; j < CPL; ++j) {
+                    const float xc = __fadd_rn((float)(tx0 + lane + 32 * j), 0.5f);
+                    xc2[j] = f2_pack(xc, xc);
+                }
+                const F2 mx = f2_pack(J.M[0], J.M[3]), my = f2_pack(J.M[1], J.M[4]), m2 = f2_pack(J.M[2], J.M[5]);
+                const F2 kq = f2_pack(2048.f, 2048.f), kt = f2_pack(8387584.5f, 8387584.5f);
+                const F2 kf = f2_pack(8388607.5f, 8388607.5f);
+                // The coordinate bits give x0 + xb (and y0 + xb); the top-left tap is word
+                // y sw + x + abase, or byte y rstride + 3 x + abase (mod 2^32).
+                const uint32_t xb = OT::is_f32 ? 0x4B000000u : (0x4B000000u >> 11);
+                const uint32_t abase = F == TAPS_RAW
+                                           ? (uint32_t)(rph - fy0 * rstride - 3 * fx0) - xb * (uint32_t)(rstride + 3)
+                                           : (uint32_t)(-(fy0 * sw + fx0)) - xb * (uint32_t)(sw + 1);
                 for (int r = warp; r < ny; r += kWarps) {
                     const float yc = __fadd_rn((float)(ty0 + r), 0.5f);
-                    const float rx = __fmaf_rn(J.M[1], yc, J.M[2]);
-                    const float ry = __fmaf_rn(J.M[4], yc, J.M[5]);
+                    const F2 rxy = f2_fma(my, f2_pack(yc, yc), m2);
                     const ORow o = orow_of(r);
 #pragma unroll
                     for (int j = 0; j < CPL; ++j) {
                         const int c = lane + 32 * j;
                         if (c < nx) {
-                            const float ax = __fmaf_rn(J.M[0], xcs[j], rx);
-                            const float ay = __fmaf_rn(J.M[3], xcs[j], ry);
-                            int x0, y0, qx = 0, qy = 0;
+                            const F2 a2 = f2_fma(mx, xc2[j], rxy);
+                            uint32_t xi, yi;
+                            int qx = 0, qy = 0;
                             float fx = 0.f, fy = 0.f;
                             if (!OT::is_f32) {
-                                const int Tx = warp_fixed_fast(ax), Ty = warp_fixed_fast(ay);
-                                x0 = Tx >> 11; qx = Tx & 2047;
-                                y0 = Ty >> 11; qy = Ty & 2047;
+                                uint32_t tx, ty;
+                                f2_unpack_bits(f2_fma_rm(a2, kq, kt), tx, ty);
+                                xi = tx >> 11; qx = (int)(tx & 2047u);
+                                yi = ty >> 11; qy = (int)(ty & 2047u);
                             } else {
-                                const float sx = __fsub_rn(ax, 0.5f), sy = __fsub_rn(ay, 0.5f);
-                                x0 = __float2int_rd(sx);
-                                y0 = __float2int_rd(sy);
-                                // exact float of x0 in [0, 2^23): 2^23 + x0 has x0 in its mantissa
-                                fx = __fsub_rn(sx, __fsub_rn(__int_as_float(0x4B000000 + x0), 8388608.f));
-                                fy = __fsub_rn(sy, __fsub_rn(__int_as_float(0x4B000000 + y0), 8388608.f));
+                                const F2 fl = f2_add_rm(a2, kf);
+                                f2_unpack(f2_sub(a2, f2_sub(fl, kf)), fx, fy);
+                                f2_unpack_bits(fl, xi, yi);
                             }
                             if (F == TAPS_RAW) {
-                                const int off = y0 * rstride + 3 * x0 + abase;
+                                const int off = (int)(yi * (uint32_t)rstride + 3u * xi + abase);
                                 const uint8_t *wp = raw + (off & ~3);
                                 const uint32_t sh = (uint32_t)off << 3;
                                 uint32_t p00, p01, p10, p11;
@@ -841,7 +863,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                                 raw_pair(wp + rstride, sh, p10, p11);
                                 emit<CIN, OUTK, F>(J, o, c, p00, p01, p10, p11, qx, qy, fx, fy);
                             } else {
-                                const uint32_t *w0 = words + (y0 * sw + x0 + abase);
+                                const uint32_t *w0 = words + (int)(yi * (uint32_t)sw + xi + abase);
                                 emit<CIN, OUTK>(J, o, c, w0[0], w0[1], w0[sw], w0[sw + 1], qx, qy, fx, fy);
                             }
                         }
