@@ -169,7 +169,7 @@ struct TileCfg {
 
 template <int TW, int TH> static constexpr int max_region_b()
 {
-    return 3 * TH * round16(TW * 4 + 15) > kRegionBCap ? 3 * TH * round16(TW * 4 + 15) : kRegionBCap;
+    return 3 * (TH / 2) * round16(TW * 4 + 15) > kRegionBCap ? 3 * (TH / 2) * round16(TW * 4 + 15) : kRegionBCap;
 }
 
 static TileCfg g_cfgs[] = {
@@ -180,11 +180,13 @@ static TileCfg g_cfgs[] = {
 };
 constexpr int kNumCfgs = sizeof(g_cfgs) / sizeof(g_cfgs[0]);
 
+// The output stage of process_tile (out_stage_bytes) for a runtime kind: f32 tiles stage
+// one band of th / 2 rows at a time.
 static int out_stage_of(int outk, int cin, int tw, int th)
 {
     const bool f32 = outk == OUT_F32 || outk == OUT_F32_GRAY;
     const int dC = (outk == OUT_U8_GRAY || outk == OUT_F32_GRAY) ? 1 : cin;
-    return f32 ? dC * th * round16(tw * 4 + 15) : th * round16(tw * dC + 15);
+    return f32 ? dC * (th / 2) * round16(tw * 4 + 15) : th * round16(tw * dC + 15);
 }
 
 // ---------------------------------------------------------------------------

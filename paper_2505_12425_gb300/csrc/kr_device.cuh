@@ -78,15 +78,22 @@ template <int OUTK, int CIN> struct OutTraits {
     static constexpr bool is_f32 = esize == 4;
 };
 
+// Output rows a tile stages at a time: f32 tiles leave in two bands of TH / 2 rows.
+template <int OUTK, int CIN, int TH>
+__host__ __device__ constexpr int out_band_rows()
+{
+    return OutTraits<OUTK, CIN>::is_f32 ? TH / 2 : TH;
+}
+
 // Shared bytes of the output staging buffer of a TW x TH tile: f32 tiles are
 // sized for three planar rows of TW floats (which also covers one HWC row of
-// 3*TW floats); u8 tiles hold TH rows of TW*dC bytes. Every row gets 15 bytes
-// of room for its 16-byte phase.
+// 3*TW floats) per band row; u8 tiles hold TH rows of TW*dC bytes. Every row
+// gets 15 bytes of room for its 16-byte phase.
 template <int OUTK, int CIN, int TW, int TH>
 __host__ __device__ constexpr int out_stage_bytes()
 {
     return OutTraits<OUTK, CIN>::is_f32
-               ? OutTraits<OUTK, CIN>::dC * TH * round16(TW * 4 + 15)
+               ? OutTraits<OUTK, CIN>::dC * out_band_rows<OUTK, CIN, TH>() * round16(TW * 4 + 15)
                : TH * round16(TW * OutTraits<OUTK, CIN>::dC + 15);
 }
 
@@ -526,7 +533,7 @@ template <int OP, int CIN, int OUTK, int TW, int TH>
 __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_y, uint8_t *smem,
                                              TileShared<TW, TH> &ts)
 {
-    static_assert(TW % 32 == 0 && TH % kWarps == 0, "tile shape");
+    static_assert(TW % 32 == 0 && TH % (2 * kWarps) == 0, "tile shape");
     using OT = OutTraits<OUTK, CIN>;
     constexpr int dC = OT::dC;
     constexpr int ES = OT::esize;
@@ -714,7 +721,10 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         }
     }
 
-    // ---- 3. compute --------------------------------------------------------------
+    // ---- 3. compute and 4. write-out, by bands of BH rows: f32 tiles leave in two bands,
+    // so that the output stage holds half a tile (more CTAs per SM).
+    constexpr int BH = out_band_rows<OUTK, CIN, TH>();
+    constexpr int NBAND = TH / BH;
     const bool chw = OT::is_f32 && dC == 3 && J.chw;
     // output rows: dense when the tile leaves through a TMA store (its rows are 16-byte
     // aligned), else with room for each row's 16-byte phase
@@ -725,137 +735,188 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     const uint32_t obase = (uint32_t)(uintptr_t)(J.dst + (int64_t)ty0 * J.dpitch +
                                                  (chw ? (int64_t)tx0 * 4 : (int64_t)tx0 * dC * ES));
     const uint32_t opitch = (uint32_t)J.dpitch, oplane = (uint32_t)J.dplane;
+    int r0 = 0;   // first tile row of the current band
     auto orow_of = [&](int r) -> ORow {
         ORow o;
         const uint32_t a = obase + (uint32_t)r * opitch;
-        o.p0 = ostage + r * orow + (a & 15u);
+        const int sr = r - r0;
+        o.p0 = ostage + sr * orow + (a & 15u);
         if (chw) {
-            o.p1 = ostage + (TH + r) * orow + ((a + oplane) & 15u);
-            o.p2 = ostage + (2 * TH + r) * orow + ((a + 2u * oplane) & 15u);
+            o.p1 = ostage + (BH + sr) * orow + ((a + oplane) & 15u);
+            o.p2 = ostage + (2 * BH + sr) * orow + ((a + 2u * oplane) & 15u);
         } else {
             o.p1 = o.p2 = nullptr;
         }
         return o;
     };
 
-    if (zero_tile) {
-        // every tap lies outside the image: every output pixel is the zero sample, which is
-        // 0 for u8 and (0 - mean[c]) / std[c] = bias[c] (bias[0] for gray) for f32
-        for (int r = warp; r < ny; r += kWarps) {
-            const ORow o = orow_of(r);
-#pragma unroll
-            for (int j = 0; j < CPL; ++j) {
-                const int c = lane + 32 * j;
-                if (c >= nx) continue;
-                if (!OT::is_f32) {
-#pragma unroll
-                    for (int k = 0; k < dC; ++k) o.p0[c * dC + k] = 0;
-                } else if (chw) {
-                    reinterpret_cast<float *>(o.p0)[c] = J.bias[0];
-                    reinterpret_cast<float *>(o.p1)[c] = J.bias[1];
-                    reinterpret_cast<float *>(o.p2)[c] = J.bias[2];
-                } else {
-#pragma unroll
-                    for (int k = 0; k < dC; ++k) reinterpret_cast<float *>(o.p0)[c * dC + k] = J.bias[k];
-                }
-            }
-        }
-    } else if (fast && CIN == 3) {
-        // Taps are addressed box-relative: word index into the re-laid box (TAPS_WORDS) or
-        // byte offset into the raw rows, every row starting at phase rph (TAPS_RAW).
-        auto fast3 = [&](auto fmt) {
-            constexpr int F = decltype(fmt)::value;
-            if (OP == OP_RESIZE) {
-                int xo[CPL], xo1[CPL], qxs[CPL];   // left tap (word index / byte offset), right tap
-                float fxs[CPL];
+    for (int band = 0; band < NBAND; ++band) {
+        r0 = band * BH;
+        if (r0 >= ny) break;
+        const int r1 = min(ny, r0 + BH);
+        if (band > 0) __syncthreads();   // the previous band has left the output stage
+
+        if (zero_tile) {
+            // every tap lies outside the image: every output pixel is the zero sample, which is
+            // 0 for u8 and (0 - mean[c]) / std[c] = bias[c] (bias[0] for gray) for f32
+            for (int r = r0 + warp; r < r1; r += kWarps) {
+                const ORow o = orow_of(r);
 #pragma unroll
                 for (int j = 0; j < CPL; ++j) {
                     const int c = lane + 32 * j;
-                    const int xr = ts.cx0[c] - fx0;
-                    xo[j] = F == TAPS_RAW ? rph + 3 * xr : xr;
-                    xo1[j] = xr + (ts.cqd[c] >> 16);
-                    qxs[j] = ts.cqd[c] & 0xFFFF;
-                    fxs[j] = ts.cf[c];
+                    if (c >= nx) continue;
+                    if (!OT::is_f32) {
+#pragma unroll
+                        for (int k = 0; k < dC; ++k) o.p0[c * dC + k] = 0;
+                    } else if (chw) {
+                        reinterpret_cast<float *>(o.p0)[c] = J.bias[0];
+                        reinterpret_cast<float *>(o.p1)[c] = J.bias[1];
+                        reinterpret_cast<float *>(o.p2)[c] = J.bias[2];
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < dC; ++k) reinterpret_cast<float *>(o.p0)[c * dC + k] = J.bias[k];
+                    }
                 }
-                for (int r = warp; r < ny; r += kWarps) {
-                    const int y0 = ts.ry0[r], qy = ts.rqd[r] & 0xFFFF, dy = ts.rqd[r] >> 16;
-                    const float fy = ts.rf[r];
-                    const ORow o = orow_of(r);
-                    if (F == TAPS_RAW) {
-                        // the pair (x0, x0 + 1) even where x1 = x0 (right edge): there q = 0
-                        const uint8_t *b0 = raw + (y0 - fy0) * rstride;
-                        const int d1 = dy * rstride;
+            }
+        } else if (fast && CIN == 3) {
+            // Taps are addressed box-relative: word index into the re-laid box (TAPS_WORDS) or
+            // byte offset into the raw rows, every row starting at phase rph (TAPS_RAW).
+            auto fast3 = [&](auto fmt) {
+                constexpr int F = decltype(fmt)::value;
+                if (OP == OP_RESIZE) {
+                    int xo[CPL], xo1[CPL], qxs[CPL];   // left tap (word index / byte offset), right tap
+                    float fxs[CPL];
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j) {
+                        const int c = lane + 32 * j;
+                        const int xr = ts.cx0[c] - fx0;
+                        xo[j] = F == TAPS_RAW ? rph + 3 * xr : xr;
+                        xo1[j] = xr + (ts.cqd[c] >> 16);
+                        qxs[j] = ts.cqd[c] & 0xFFFF;
+                        fxs[j] = ts.cf[c];
+                    }
+                    for (int r = r0 + warp; r < r1; r += kWarps) {
+                        const int y0 = ts.ry0[r], qy = ts.rqd[r] & 0xFFFF, dy = ts.rqd[r] >> 16;
+                        const float fy = ts.rf[r];
+                        const ORow o = orow_of(r);
+                        if (F == TAPS_RAW) {
+                            // the pair (x0, x0 + 1) even where x1 = x0 (right edge): there q = 0
+                            const uint8_t *b0 = raw + (y0 - fy0) * rstride;
+                            const int d1 = dy * rstride;
+#pragma unroll
+                            for (int j = 0; j < CPL; ++j) {
+                                const int c = lane + 32 * j;
+                                if (c < nx) {
+                                    uint32_t p00, p01, p10, p11;
+                                    const uint8_t *wp = b0 + (xo[j] & ~3);
+                                    const uint32_t sh = (uint32_t)xo[j] << 3;
+                                    raw_pair(wp, sh, p00, p01);
+                                    raw_pair(wp + d1, sh, p10, p11);
+                                    emit<CIN, OUTK, F>(J, o, c, p00, p01, p10, p11, qxs[j], qy, fxs[j], fy);
+                                }
+                            }
+                        } else {
+                            const uint32_t *w0 = words + (y0 - fy0) * sw;
+                            const uint32_t *w1 = w0 + dy * sw;
+#pragma unroll
+                            for (int j = 0; j < CPL; ++j) {
+                                const int c = lane + 32 * j;
+                                if (c < nx)
+                                    emit<CIN, OUTK>(J, o, c, w0[xo[j]], w0[xo1[j]], w1[xo[j]], w1[xo1[j]], qxs[j], qy,
+                                                    fxs[j], fy);
+                            }
+                        }
+                    }
+                } else {
+                    // warp: (ax, ay) = (m00, m10) (x + 1/2) + row terms, the two axes in one packed
+                    // lane pair (fp32 fmas, lane by lane as in the definition), then the fast forms,
+                    // both rounded toward minus infinity (exact on [0, 4094), checked exhaustively
+                    // on the host):
+                    //   u8   fma(a, 2048, 2^23 - 1023.5) = 2^23 + 2048 x0 + q  (bits 0x4B000000 + ..;
+                    //        q = 2048 comes out as x0 + 1 with q = 0, the same sample)
+                    //   f32  a + (2^23 - 1/2) = 2^23 + x0; the weight of x0 + 1 is a - (x0 + 1/2)
+                    F2 xc2[CPL];
+#pragma unroll
+                    for (int j = 0; j < CPL; ++j) {
+                        const float xc = __fadd_rn((float)(tx0 + lane + 32 * j), 0.5f);
+                        xc2[j] = f2_pack(xc, xc);
+                    }
+                    const F2 mx = f2_pack(J.M[0], J.M[3]), my = f2_pack(J.M[1], J.M[4]), m2 = f2_pack(J.M[2], J.M[5]);
+                    const F2 kq = f2_pack(2048.f, 2048.f), kt = f2_pack(8387584.5f, 8387584.5f);
+                    const F2 kf = f2_pack(8388607.5f, 8388607.5f);
+                    // The coordinate bits give x0 + xb (and y0 + xb); the top-left tap is word
+                    // y sw + x + abase, or byte y rstride + 3 x + abase (mod 2^32).
+                    const uint32_t xb = OT::is_f32 ? 0x4B000000u : (0x4B000000u >> 11);
+                    const uint32_t abase = F == TAPS_RAW
+                                               ? (uint32_t)(rph - fy0 * rstride - 3 * fx0) - xb * (uint32_t)(rstride + 3)
+                                               : (uint32_t)(-(fy0 * sw + fx0)) - xb * (uint32_t)(sw + 1);
+                    for (int r = r0 + warp; r < r1; r += kWarps) {
+                        const float yc = __fadd_rn((float)(ty0 + r), 0.5f);
+                        const F2 rxy = f2_fma(my, f2_pack(yc, yc), m2);
+                        const ORow o = orow_of(r);
 #pragma unroll
                         for (int j = 0; j < CPL; ++j) {
                             const int c = lane + 32 * j;
                             if (c < nx) {
-                                uint32_t p00, p01, p10, p11;
-                                const uint8_t *wp = b0 + (xo[j] & ~3);
-                                const uint32_t sh = (uint32_t)xo[j] << 3;
-                                raw_pair(wp, sh, p00, p01);
-                                raw_pair(wp + d1, sh, p10, p11);
-                                emit<CIN, OUTK, F>(J, o, c, p00, p01, p10, p11, qxs[j], qy, fxs[j], fy);
+                                const F2 a2 = f2_fma(mx, xc2[j], rxy);
+                                uint32_t xi, yi;
+                                int qx = 0, qy = 0;
+                                float fx = 0.f, fy = 0.f;
+                                if (!OT::is_f32) {
+                                    uint32_t tx, ty;
+                                    f2_unpack_bits(f2_fma_rm(a2, kq, kt), tx, ty);
+                                    xi = tx >> 11; qx = (int)(tx & 2047u);
+                                    yi = ty >> 11; qy = (int)(ty & 2047u);
+                                } else {
+                                    const F2 fl = f2_add_rm(a2, kf);
+                                    f2_unpack(f2_sub(a2, f2_sub(fl, kf)), fx, fy);
+                                    f2_unpack_bits(fl, xi, yi);
+                                }
+                                if (F == TAPS_RAW) {
+                                    const int off = (int)(yi * (uint32_t)rstride + 3u * xi + abase);
+                                    const uint8_t *wp = raw + (off & ~3);
+                                    const uint32_t sh = (uint32_t)off << 3;
+                                    uint32_t p00, p01, p10, p11;
+                                    raw_pair(wp, sh, p00, p01);
+                                    raw_pair(wp + rstride, sh, p10, p11);
+                                    emit<CIN, OUTK, F>(J, o, c, p00, p01, p10, p11, qx, qy, fx, fy);
+                                } else {
+                                    const uint32_t *w0 = words + (int)(yi * (uint32_t)sw + xi + abase);
+                                    emit<CIN, OUTK>(J, o, c, w0[0], w0[1], w0[sw], w0[sw + 1], qx, qy, fx, fy);
+                                }
                             }
-                        }
-                    } else {
-                        const uint32_t *w0 = words + (y0 - fy0) * sw;
-                        const uint32_t *w1 = w0 + dy * sw;
-#pragma unroll
-                        for (int j = 0; j < CPL; ++j) {
-                            const int c = lane + 32 * j;
-                            if (c < nx)
-                                emit<CIN, OUTK>(J, o, c, w0[xo[j]], w0[xo1[j]], w1[xo[j]], w1[xo1[j]], qxs[j], qy,
-                                                fxs[j], fy);
                         }
                     }
                 }
-            } else {
-                // warp: (ax, ay) = (m00, m10) (x + 1/2) + row terms, the two axes in one packed
-                // lane pair (fp32 fmas, lane by lane as in the definition), then the fast forms,
-                // both rounded toward minus infinity (exact on [0, 4094), checked exhaustively
-                // on the host):
-                //   u8   fma(a, 2048, 2^23 - 1023.5) = 2^23 + 2048 x0 + q  (bits 0x4B000000 + ..;
-                //        q = 2048 comes out as x0 + 1 with q = 0, the same sample)
-                //   f32  a + (2^23 - 1/2) = 2^23 + x0; the weight of x0 + 1 is a - (x0 + 1/2)
-                F2 xc2[CPL];
-#pragma unroll
-                for (int j = 0; j < CPL; ++j) {
-                    const float xc = __fadd_rn((float)(tx0 + lane + 32 * j), 0.5f);
-                    xc2[j] = f2_pack(xc, xc);
-                }
-                const F2 mx = f2_pack(J.M[0], J.M[3]), my = f2_pack(J.M[1], J.M[4]), m2 = f2_pack(J.M[2], J.M[5]);
-                const F2 kq = f2_pack(2048.f, 2048.f), kt = f2_pack(8387584.5f, 8387584.5f);
-                const F2 kf = f2_pack(8388607.5f, 8388607.5f);
-                // The coordinate bits give x0 + xb (and y0 + xb); the top-left tap is word
-                // y sw + x + abase, or byte y rstride + 3 x + abase (mod 2^32).
-                const uint32_t xb = OT::is_f32 ? 0x4B000000u : (0x4B000000u >> 11);
-                const uint32_t abase = F == TAPS_RAW
-                                           ? (uint32_t)(rph - fy0 * rstride - 3 * fx0) - xb * (uint32_t)(rstride + 3)
-                                           : (uint32_t)(-(fy0 * sw + fx0)) - xb * (uint32_t)(sw + 1);
-                for (int r = warp; r < ny; r += kWarps) {
+            };
+            if (rawbox) fast3(IntC<TAPS_RAW>{}); else fast3(IntC<TAPS_WORDS>{});
+        } else if (OP == OP_WARP && CIN == 3 && staged) {
+            // Medium path (warp tiles with coordinates outside [0, 4094)): the exact weight
+            // formula per pixel; every tap still lies in the zero-filled box.
+            auto medium3 = [&](auto fmt) {
+                constexpr int F = decltype(fmt)::value;
+                for (int r = r0 + warp; r < r1; r += kWarps) {
                     const float yc = __fadd_rn((float)(ty0 + r), 0.5f);
-                    const F2 rxy = f2_fma(my, f2_pack(yc, yc), m2);
+                    const float rx = __fmaf_rn(J.M[1], yc, J.M[2]);
+                    const float ry = __fmaf_rn(J.M[4], yc, J.M[5]);
                     const ORow o = orow_of(r);
 #pragma unroll
                     for (int j = 0; j < CPL; ++j) {
                         const int c = lane + 32 * j;
                         if (c < nx) {
-                            const F2 a2 = f2_fma(mx, xc2[j], rxy);
-                            uint32_t xi, yi;
-                            int qx = 0, qy = 0;
+                            const float xc = __fadd_rn((float)(tx0 + c), 0.5f);
+                            const float sx = __fsub_rn(__fmaf_rn(J.M[0], xc, rx), 0.5f);
+                            const float sy = __fsub_rn(__fmaf_rn(J.M[3], xc, ry), 0.5f);
+                            int x0, y0, qx, qy;
+                            warp_weight(sx, x0, qx);
+                            warp_weight(sy, y0, qy);
                             float fx = 0.f, fy = 0.f;
-                            if (!OT::is_f32) {
-                                uint32_t tx, ty;
-                                f2_unpack_bits(f2_fma_rm(a2, kq, kt), tx, ty);
-                                xi = tx >> 11; qx = (int)(tx & 2047u);
-                                yi = ty >> 11; qy = (int)(ty & 2047u);
-                            } else {
-                                const F2 fl = f2_add_rm(a2, kf);
-                                f2_unpack(f2_sub(a2, f2_sub(fl, kf)), fx, fy);
-                                f2_unpack_bits(fl, xi, yi);
+                            if (OT::is_f32) {
+                                fx = __fsub_rn(sx, floorf(sx));
+                                fy = __fsub_rn(sy, floorf(sy));
                             }
                             if (F == TAPS_RAW) {
-                                const int off = (int)(yi * (uint32_t)rstride + 3u * xi + abase);
+                                const int off = (y0 - fy0) * rstride + 3 * (x0 - fx0) + rph;
                                 const uint8_t *wp = raw + (off & ~3);
                                 const uint32_t sh = (uint32_t)off << 3;
                                 uint32_t p00, p01, p10, p11;
@@ -863,188 +924,146 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                                 raw_pair(wp + rstride, sh, p10, p11);
                                 emit<CIN, OUTK, F>(J, o, c, p00, p01, p10, p11, qx, qy, fx, fy);
                             } else {
-                                const uint32_t *w0 = words + (int)(yi * (uint32_t)sw + xi + abase);
+                                const uint32_t *w0 = words + ((y0 - fy0) * sw + (x0 - fx0));
                                 emit<CIN, OUTK>(J, o, c, w0[0], w0[1], w0[sw], w0[sw + 1], qx, qy, fx, fy);
                             }
                         }
                     }
                 }
-            }
-        };
-        if (rawbox) fast3(IntC<TAPS_RAW>{}); else fast3(IntC<TAPS_WORDS>{});
-    } else if (OP == OP_WARP && CIN == 3 && staged) {
-        // Medium path (warp tiles with coordinates outside [0, 4094)): the exact weight
-        // formula per pixel; every tap still lies in the zero-filled box.
-        auto medium3 = [&](auto fmt) {
-            constexpr int F = decltype(fmt)::value;
-            for (int r = warp; r < ny; r += kWarps) {
-                const float yc = __fadd_rn((float)(ty0 + r), 0.5f);
-                const float rx = __fmaf_rn(J.M[1], yc, J.M[2]);
-                const float ry = __fmaf_rn(J.M[4], yc, J.M[5]);
+            };
+            if (rawbox) medium3(IntC<TAPS_RAW>{}); else medium3(IntC<TAPS_WORDS>{});
+        } else {
+            // General path: per-pixel coordinates with the full rules; taps from the
+            // staged box when inside it, else from global memory (zero outside the image).
+            const uint32_t rowphase0 = (uint32_t)(uintptr_t)(J.src + (int64_t)fx0 * CIN);
+            for (int r = r0 + warp; r < r1; r += kWarps) {
+                const int y = ty0 + r;
                 const ORow o = orow_of(r);
-#pragma unroll
                 for (int j = 0; j < CPL; ++j) {
                     const int c = lane + 32 * j;
-                    if (c < nx) {
-                        const float xc = __fadd_rn((float)(tx0 + c), 0.5f);
-                        const float sx = __fsub_rn(__fmaf_rn(J.M[0], xc, rx), 0.5f);
-                        const float sy = __fsub_rn(__fmaf_rn(J.M[3], xc, ry), 0.5f);
-                        int x0, y0, qx, qy;
-                        warp_weight(sx, x0, qx);
-                        warp_weight(sy, y0, qy);
-                        float fx = 0.f, fy = 0.f;
-                        if (OT::is_f32) {
+                    if (c >= nx) continue;
+                    const int x = tx0 + c;
+                    int x0 = 0, y0 = 0, qx = 0, qy = 0, dx = 1, dy = 1;
+                    float fx = 0.f, fy = 0.f;
+                    bool valid = true;
+                    if (OP == OP_RESIZE) {
+                        x0 = ts.cx0[c]; dx = ts.cqd[c] >> 16; qx = ts.cqd[c] & 0xFFFF; fx = ts.cf[c];
+                        y0 = ts.ry0[r]; dy = ts.rqd[r] >> 16; qy = ts.rqd[r] & 0xFFFF; fy = ts.rf[r];
+                    } else {
+                        float sx, sy;
+                        valid = warp_coord(J.M, x, y, sx, sy);
+                        if (valid) {
+                            warp_weight(sx, x0, qx);
+                            warp_weight(sy, y0, qy);
                             fx = __fsub_rn(sx, floorf(sx));
                             fy = __fsub_rn(sy, floorf(sy));
                         }
-                        if (F == TAPS_RAW) {
-                            const int off = (y0 - fy0) * rstride + 3 * (x0 - fx0) + rph;
-                            const uint8_t *wp = raw + (off & ~3);
-                            const uint32_t sh = (uint32_t)off << 3;
-                            uint32_t p00, p01, p10, p11;
-                            raw_pair(wp, sh, p00, p01);
-                            raw_pair(wp + rstride, sh, p10, p11);
-                            emit<CIN, OUTK, F>(J, o, c, p00, p01, p10, p11, qx, qy, fx, fy);
-                        } else {
+                    }
+                    uint32_t p00 = 0, p01 = 0, p10 = 0, p11 = 0;
+                    if (valid) {
+                        const bool in_box = staged && x0 >= fx0 && x0 + dx <= fx1 && y0 >= fy0 && y0 + dy <= fy1;
+                        // (3-channel tiles get here only unstaged: staged ones take the fast or
+                        // medium path)
+                        if (in_box && CIN == 3) {
                             const uint32_t *w0 = words + ((y0 - fy0) * sw + (x0 - fx0));
-                            emit<CIN, OUTK>(J, o, c, w0[0], w0[1], w0[sw], w0[sw + 1], qx, qy, fx, fy);
+                            const uint32_t *w1 = w0 + dy * sw;
+                            p00 = w0[0]; p01 = w0[dx]; p10 = w1[0]; p11 = w1[dx];
+                        } else if (in_box) {
+                            const int r0 = y0 - fy0, r1 = r0 + dy;
+                            const int ph0 = (int)((rowphase0 + (uint32_t)((int64_t)y0 * J.spitch)) & 15u);
+                            const int ph1 = (int)((rowphase0 + (uint32_t)((int64_t)(y0 + dy) * J.spitch)) & 15u);
+                            const uint8_t *s0 = raw + r0 * rstride + ph0 + (x0 - fx0);
+                            const uint8_t *s1 = raw + r1 * rstride + ph1 + (x0 - fx0);
+                            p00 = s0[0]; p01 = s0[dx]; p10 = s1[0]; p11 = s1[dx];
+                        } else if (CIN == 3) {
+                            p00 = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0);
+                            p01 = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0 + dx);
+                            p10 = ldg_px3(J.src, J.spitch, J.H, J.W, y0 + dy, x0);
+                            p11 = ldg_px3(J.src, J.spitch, J.H, J.W, y0 + dy, x0 + dx);
+                        } else {
+                            p00 = ldg_px1(J.src, J.spitch, J.H, J.W, y0, x0);
+                            p01 = ldg_px1(J.src, J.spitch, J.H, J.W, y0, x0 + dx);
+                            p10 = ldg_px1(J.src, J.spitch, J.H, J.W, y0 + dy, x0);
+                            p11 = ldg_px1(J.src, J.spitch, J.H, J.W, y0 + dy, x0 + dx);
                         }
                     }
+                    emit<CIN, OUTK>(J, o, c, p00, p01, p10, p11, qx, qy, fx, fy);
                 }
             }
-        };
-        if (rawbox) medium3(IntC<TAPS_RAW>{}); else medium3(IntC<TAPS_WORDS>{});
-    } else {
-        // General path: per-pixel coordinates with the full rules; taps from the
-        // staged box when inside it, else from global memory (zero outside the image).
-        const uint32_t rowphase0 = (uint32_t)(uintptr_t)(J.src + (int64_t)fx0 * CIN);
-        for (int r = warp; r < ny; r += kWarps) {
-            const int y = ty0 + r;
-            const ORow o = orow_of(r);
-            for (int j = 0; j < CPL; ++j) {
-                const int c = lane + 32 * j;
-                if (c >= nx) continue;
-                const int x = tx0 + c;
-                int x0 = 0, y0 = 0, qx = 0, qy = 0, dx = 1, dy = 1;
-                float fx = 0.f, fy = 0.f;
-                bool valid = true;
-                if (OP == OP_RESIZE) {
-                    x0 = ts.cx0[c]; dx = ts.cqd[c] >> 16; qx = ts.cqd[c] & 0xFFFF; fx = ts.cf[c];
-                    y0 = ts.ry0[r]; dy = ts.rqd[r] >> 16; qy = ts.rqd[r] & 0xFFFF; fy = ts.rf[r];
+        }
+        if (tma_out) fence_proxy_async_smem();
+        __syncthreads();
+
+        if (tma_out) {
+            // write-out through TMA stores of the band (rows and chunks past the image's edge
+            // are clipped by the copy engine)
+            if (tid == 0) {
+                if (chw) {
+                    for (int pl = 0; pl < 3; ++pl)
+                        tma_store_4d(J.tout, tx0, ty0 + r0, pl, J.zimg, ostage + pl * BH * orow);
                 } else {
-                    float sx, sy;
-                    valid = warp_coord(J.M, x, y, sx, sy);
-                    if (valid) {
-                        warp_weight(sx, x0, qx);
-                        warp_weight(sy, y0, qy);
-                        fx = __fsub_rn(sx, floorf(sx));
-                        fy = __fsub_rn(sy, floorf(sy));
-                    }
+                    tma_store_3d(J.tout, (tx0 * dC * ES) >> 2, ty0 + r0, J.zimg, ostage);
                 }
-                uint32_t p00 = 0, p01 = 0, p10 = 0, p11 = 0;
-                if (valid) {
-                    const bool in_box = staged && x0 >= fx0 && x0 + dx <= fx1 && y0 >= fy0 && y0 + dy <= fy1;
-                    // (3-channel tiles get here only unstaged: staged ones take the fast or
-                    // medium path)
-                    if (in_box && CIN == 3) {
-                        const uint32_t *w0 = words + ((y0 - fy0) * sw + (x0 - fx0));
-                        const uint32_t *w1 = w0 + dy * sw;
-                        p00 = w0[0]; p01 = w0[dx]; p10 = w1[0]; p11 = w1[dx];
-                    } else if (in_box) {
-                        const int r0 = y0 - fy0, r1 = r0 + dy;
-                        const int ph0 = (int)((rowphase0 + (uint32_t)((int64_t)y0 * J.spitch)) & 15u);
-                        const int ph1 = (int)((rowphase0 + (uint32_t)((int64_t)(y0 + dy) * J.spitch)) & 15u);
-                        const uint8_t *s0 = raw + r0 * rstride + ph0 + (x0 - fx0);
-                        const uint8_t *s1 = raw + r1 * rstride + ph1 + (x0 - fx0);
-                        p00 = s0[0]; p01 = s0[dx]; p10 = s1[0]; p11 = s1[dx];
-                    } else if (CIN == 3) {
-                        p00 = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0);
-                        p01 = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0 + dx);
-                        p10 = ldg_px3(J.src, J.spitch, J.H, J.W, y0 + dy, x0);
-                        p11 = ldg_px3(J.src, J.spitch, J.H, J.W, y0 + dy, x0 + dx);
-                    } else {
-                        p00 = ldg_px1(J.src, J.spitch, J.H, J.W, y0, x0);
-                        p01 = ldg_px1(J.src, J.spitch, J.H, J.W, y0, x0 + dx);
-                        p10 = ldg_px1(J.src, J.spitch, J.H, J.W, y0 + dy, x0);
-                        p11 = ldg_px1(J.src, J.spitch, J.H, J.W, y0 + dy, x0 + dx);
-                    }
-                }
-                emit<CIN, OUTK>(J, o, c, p00, p01, p10, p11, qx, qy, fx, fy);
+                tma_store_commit_and_wait_read();
             }
+            // After the last band no closing barrier: this path runs one tile per CTA, the
+            // storing thread waits for the copy engine to finish reading the stage, and a
+            // CTA's shared memory lives until its last thread exits.
+            if (r1 >= ny) return;
+            continue;
         }
-    }
-    if (tma_out) fence_proxy_async_smem();
-    __syncthreads();
 
-    if (tma_out) {
-        // ---- 4. write-out through TMA stores of the whole tile (rows and chunks past the
-        // image's edge are clipped by the copy engine).
-        if (tid == 0) {
-            if (chw) {
-                for (int pl = 0; pl < 3; ++pl)
-                    tma_store_4d(J.tout, tx0, ty0, pl, J.zimg, ostage + pl * TH * orow);
-            } else {
-                tma_store_3d(J.tout, (tx0 * dC * ES) >> 2, ty0, J.zimg, ostage);
-            }
-            tma_store_commit_and_wait_read();
-        }
-        // No closing barrier: this path runs one tile per CTA, the storing thread waits for
-        // the copy engine to finish reading the tile, and a CTA's shared memory lives until
-        // its last thread exits.
-        return;
-    }
-
-    // ---- 4. write-out: 16-byte chunks of every (plane, row) segment spread over the
-    // CTA; a second pass, only when some row is not 16-byte aligned at both ends,
-    // moves the (at most 15 + 15) head and tail bytes of each segment, one per thread.
-    const int nplanes = chw ? 3 : 1;
-    const int seglen = chw ? nx * 4 : nx * dC * ES;
-    const int nseg = nplanes * ny;
-    const int ncs = (seglen + 15 + 15) >> 4;           // chunks a segment can span
-    const float inv_ncs = __frcp_rn((float)ncs);
-    const int64_t tile_off = chw ? (int64_t)tx0 * 4 : (int64_t)tx0 * dC * ES;
-    uint8_t *drow0 = J.dst + (int64_t)ty0 * J.dpitch + tile_off;
-    auto seg_base = [&](int sidx, int &r) -> uint8_t * {
-        const int pl = chw ? (sidx >= ny) + (sidx >= 2 * ny) : 0;
-        r = sidx - pl * ny;
-        return drow0 + (int64_t)r * J.dpitch + (int64_t)pl * J.dplane;
-    };
-    for (int i = tid; i < nseg * ncs; i += kThreads) {
-        const int sidx = (int)__fmul_rz((float)i + 0.5f, inv_ncs);
-        const int j = i - sidx * ncs;
-        int r;
-        uint8_t *g = seg_base(sidx, r);
-        const int phase = (int)((uintptr_t)g & 15);
-        const int b0 = 16 * j;
-        if (b0 >= phase && b0 + 16 <= phase + seglen) {
-            const int pl = chw ? (sidx >= ny) + (sidx >= 2 * ny) : 0;
-            *reinterpret_cast<uint4 *>(g - phase + b0) =
-                *reinterpret_cast<const uint4 *>(ostage + (pl * TH + r) * orow + b0);
-        }
-    }
-    const bool aligned_rows = ((obase | opitch | (chw ? oplane : 0u) | (uint32_t)seglen) & 15u) == 0;
-    if (!aligned_rows) {
-        for (int i = tid; i < nseg * 32; i += kThreads) {
-            const int sidx = i >> 5, k = i & 31;
-            int r;
-            uint8_t *g = seg_base(sidx, r);
-            const int pl = chw ? (sidx >= ny) + (sidx >= 2 * ny) : 0;
+        // write-out: 16-byte chunks of every (plane, row) segment of the band spread over the
+        // CTA; a second pass, only when some row is not 16-byte aligned at both ends, moves
+        // the (at most 15 + 15) head and tail bytes of each segment, one per thread.
+        const int nplanes = chw ? 3 : 1;
+        const int nrow = r1 - r0;
+        const int seglen = chw ? nx * 4 : nx * dC * ES;
+        const int nseg = nplanes * nrow;
+        const int ncs = (seglen + 15 + 15) >> 4;           // chunks a segment can span
+        const float inv_ncs = __frcp_rn((float)ncs);
+        const int64_t tile_off = chw ? (int64_t)tx0 * 4 : (int64_t)tx0 * dC * ES;
+        uint8_t *drow0 = J.dst + (int64_t)(ty0 + r0) * J.dpitch + tile_off;
+        // segment sidx = (plane, band row rr): its global start and its stage row
+        auto seg_base = [&](int sidx, int &srow_off) -> uint8_t * {
+            const int pl = chw ? (sidx >= nrow) + (sidx >= 2 * nrow) : 0;
+            const int rr = sidx - pl * nrow;
+            srow_off = (pl * BH + rr) * orow;
+            return drow0 + (int64_t)rr * J.dpitch + (int64_t)pl * J.dplane;
+        };
+        for (int i = tid; i < nseg * ncs; i += kThreads) {
+            const int sidx = (int)__fmul_rz((float)i + 0.5f, inv_ncs);
+            const int j = i - sidx * ncs;
+            int so;
+            uint8_t *g = seg_base(sidx, so);
             const int phase = (int)((uintptr_t)g & 15);
-            const int end = phase + seglen;
-            const int jf = (phase + 15) >> 4, jl = end >> 4;   // full chunks: [jf, jl)
-            int b;
-            if (k < 16) {
-                b = phase + k;
-                if (b >= min(jf * 16, end)) continue;
-            } else {
-                if (jl < jf) continue;
-                b = jl * 16 + (k - 16);
-                if (b >= end) continue;
-            }
-            g[b - phase] = ostage[(pl * TH + r) * orow + b];
+            const int b0 = 16 * j;
+            if (b0 >= phase && b0 + 16 <= phase + seglen)
+                *reinterpret_cast<uint4 *>(g - phase + b0) = *reinterpret_cast<const uint4 *>(ostage + so + b0);
         }
+        const bool aligned_rows = ((obase | opitch | (chw ? oplane : 0u) | (uint32_t)seglen) & 15u) == 0;
+        if (!aligned_rows) {
+            for (int i = tid; i < nseg * 32; i += kThreads) {
+                const int sidx = i >> 5, k = i & 31;
+                int so;
+                uint8_t *g = seg_base(sidx, so);
+                const int phase = (int)((uintptr_t)g & 15);
+                const int end = phase + seglen;
+                const int jf = (phase + 15) >> 4, jl = end >> 4;   // full chunks: [jf, jl)
+                int b;
+                if (k < 16) {
+                    b = phase + k;
+                    if (b >= min(jf * 16, end)) continue;
+                } else {
+                    if (jl < jf) continue;
+                    b = jl * 16 + (k - 16);
+                    if (b >= end) continue;
+                }
+                g[b - phase] = ostage[so + b];
+            }
+        }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 }  // namespace kr

@@ -278,7 +278,7 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
         }
         p.foot_budget = bud.a;
         p.region_b = bud.b;
-        // TMA destination map: whole tiles, when every row is a whole number of 16-byte chunks
+        // TMA destination map: one band of a tile, when every row is a whole number of 16-byte chunks
         p.has_tout = 0;
         constexpr int dC = OutTraits<OUTK, CIN>::dC, ES = OutTraits<OUTK, CIN>::esize;
         const bool chw = d.chw != 0;
@@ -286,7 +286,7 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
         if (orowb % 16 == 0) {
             const int tile_chunks = chw ? TW * 4 / 16 : TW * dC * ES / 16;
             p.has_tout = encode_map(&p.tout, p.dst, orowb, d.h, chw ? 3 : 1, nb, d.dpitch, d.dplane, d.dbatch,
-                                    tile_chunks, TH) ? 1 : 0;
+                                    tile_chunks, out_band_rows<OUTK, CIN, TH>()) ? 1 : 0;
         }
         const size_t smem = (size_t)bud.a + bud.b;
         dim3 grid(tiles_x, tiles_y, nb);
