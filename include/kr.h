@@ -316,9 +316,10 @@ const char *kr_status_string(kr_status status);
 const char *kr_last_error(void);
 
 /*
- * Device-side error flags of the single-image kernels, read synchronously (the
- * current device). Bit 0: a bounded wait for a TMA copy ran out (the tile was
- * skipped and its output left unwritten). clear != 0 resets the flags.
+ * Device-side error flags of the single-image and ragged kernels, read
+ * synchronously (the current device). Bit 0: a bounded wait for a tile's
+ * staging copy (TMA or bulk row copies) ran out (the tile was skipped and its
+ * output left unwritten). clear != 0 resets the flags.
  */
 #define KR_DEVERR_TMA_TIMEOUT 1u
 kr_status kr_device_errors(uint32_t *flags, int32_t clear);

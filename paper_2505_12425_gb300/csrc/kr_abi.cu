@@ -223,8 +223,10 @@ const char *kr_last_error(void) { return g_last_error; }
 kr_status kr_device_errors(uint32_t *flags, int32_t clear)
 {
     if (!flags) return KR_ERR_INVALID_ARG;
-    unsigned v = 0;
+    unsigned v = 0, vb = 0;
     cudaError_t e = device_error_flags(&v, clear != 0);
+    if (e == cudaSuccess) e = batch_error_flags(&vb, clear != 0);
+    v |= vb;
     if (e != cudaSuccess) {
         set_last_error("kr_device_errors", e);
         return KR_ERR_CUDA;

@@ -40,7 +40,7 @@ struct alignas(16) WorkItem {
     int32_t foot_budget;
     int32_t region_b;
     int32_t chw;
-    int32_t allow_fast;
+    int32_t flags;         // ITEM_* below
     float M[6];
     float scale[3], bias[3];
 };
@@ -56,6 +56,12 @@ static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
 
 constexpr int kind_of(int op, int cin, int outk) { return op | (cin << 4) | (outk << 8); }
 constexpr int KIND_GRAY = 0x1000;
+// item flags: the warp map allows the fast path; region A is sized for raw boxes; the
+// source rows are 16-byte aligned (bulk row copies)
+constexpr int ITEM_FAST = 1, ITEM_RAW = 2, ITEM_ROWS16 = 4;
+
+// Device error flags of the ragged kernel (bit 0: a bounded staging wait ran out).
+static __device__ unsigned g_kr_batch_err;
 
 static constexpr size_t prefix_bytes(int n) { return ((size_t)(n + 1) * 4 + 15) & ~(size_t)15; }
 static constexpr size_t worklist_bytes(int n)
@@ -91,13 +97,14 @@ __device__ __forceinline__ Job job_of(const WorkItem &it)
     J.chw = it.chw;
     J.foot_budget = it.foot_budget;
     J.region_b = it.region_b;
-    J.allow_fast = it.allow_fast;
+    J.allow_fast = (it.flags & ITEM_FAST) ? 1 : 0;
     J.tin = nullptr;
     J.tin_nc = J.tin_br = 0;
-    J.raw_taps = 0;
+    J.raw_taps = (it.flags & ITEM_RAW) ? 1 : 0;
+    J.rows16 = (it.flags & ITEM_ROWS16) ? 1 : 0;
     J.tout = nullptr;
     J.zimg = 0;
-    J.err = nullptr;
+    J.err = &g_kr_batch_err;
 #pragma unroll
     for (int k = 0; k < 6; ++k) J.M[k] = it.M[k];
 #pragma unroll
@@ -118,6 +125,7 @@ __global__ void __launch_bounds__(kThreads) ragged_kernel(uint8_t *ws)
     const WorkItem *items = reinterpret_cast<const WorkItem *>(ws + sizeof(WsHeader));
     const int n = hdr->n, total = hdr->total_tiles;
     const int *prefix = reinterpret_cast<const int *>(items + n);
+    tile_shared_init(ts);
     for (;;) {
         if (threadIdx.x == 0) s_tile = (int)atomicAdd(&hdr->next, 1u);
         __syncthreads();
@@ -137,7 +145,7 @@ __global__ void __launch_bounds__(kThreads) ragged_kernel(uint8_t *ws)
             const Job J = job_of(it);
             switch (it.kind) {
 #define KR_CASE(OP, CIN, OUTK) \
-    case kind_of(OP, CIN, OUTK): process_tile<OP, CIN, OUTK, TW, TH>(J, tx, ty, smem, ts); break;
+    case kind_of(OP, CIN, OUTK): process_tile<OP, CIN, OUTK, TW, TH, true, false>(J, tx, ty, smem, ts); break;
             KR_CASE(OP_RESIZE, 3, OUT_U8)
             KR_CASE(OP_RESIZE, 3, OUT_U8_GRAY)
             KR_CASE(OP_RESIZE, 3, OUT_F32)
@@ -155,7 +163,20 @@ __global__ void __launch_bounds__(kThreads) ragged_kernel(uint8_t *ws)
             }
         }
         __syncthreads();   // everyone has read s_tile before thread 0 rewrites it
+        // a staging wait ran out twice: copies may still be in flight into this CTA's shared
+        // memory, so it takes no further tiles (the others finish the list; error bit set)
+        if (!ts.mbar_ok) break;
     }
+}
+
+cudaError_t batch_error_flags(unsigned *flags, bool clear)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(flags, g_kr_batch_err, sizeof(unsigned));
+    if (e == cudaSuccess && clear) {
+        const unsigned zero = 0;
+        e = cudaMemcpyToSymbol(g_kr_batch_err, &zero, sizeof(unsigned));
+    }
+    return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -232,11 +253,23 @@ static kr_status pack_into(const kr_work_t *items, int n, int tw, int th, WorkIt
             for (int k = 0; k < 6; ++k) it.M[k] = op == OP_WARP ? w.M[k] : 0.f;
             for (int k = 0; k < 3; ++k) { it.scale[k] = d.scale[k]; it.bias[k] = d.bias[k]; }
             const int ob = out_stage_of(d.outk, d.cin, tw, th);
-            const Budget bud = op == OP_RESIZE ? budget_resize(d.cin, d.H, d.W, d.h, d.w, tw, th, ob)
-                                               : budget_warp(d.cin, d.H, d.W, it.M, tw, th, ob);
+            Budget bud = op == OP_RESIZE ? budget_resize(d.cin, d.H, d.W, d.h, d.w, tw, th, ob)
+                                         : budget_warp(d.cin, d.H, d.W, it.M, tw, th, ob);
+            it.flags = (op == OP_RESIZE || warp_allows_fast(it.M, d.h, d.w)) ? ITEM_FAST : 0;
+            const bool rows16 = ((uintptr_t)d.src & 15) == 0 && (d.spitch & 15) == 0;
+            if (rows16) it.flags |= ITEM_ROWS16;
+            if (d.cin == 3 && rows16 && bud.a > 0 && bud.fits) {
+                // bulk row copies and raw taps: region A holds the item's largest box (plus
+                // the 16 bytes a last pixel pair may touch), region B only the output tile
+                const long long a = 16LL * ((15 + bud.cols * 3 + 15) / 16) * bud.rows + 16;
+                if (a <= std::max<long long>(bud.b, kRegionBCap)) {
+                    it.flags |= ITEM_RAW;
+                    bud.a = round128((int)a);
+                    bud.b = round16(ob);
+                }
+            }
             it.foot_budget = bud.a;
             it.region_b = bud.b;
-            it.allow_fast = op == OP_RESIZE ? 1 : (warp_allows_fast(it.M, d.h, d.w) ? 1 : 0);
             P.smem = std::max(P.smem, (size_t)bud.a + bud.b);
         } else {
             return KR_ERR_INVALID_ARG;

@@ -54,8 +54,9 @@ struct Job {
     int32_t foot_budget;  // shared bytes of region A (staged box); 0 = never stage
     int32_t region_b;     // shared bytes of region B (raw rows of 3-channel boxes, then output tile)
     int32_t allow_fast;   // warp: the map's intermediate terms are small enough for the fast path
-    int32_t raw_taps;     // 3-channel tiles staged by TMA read their taps from the raw rows in
-                          // region A (sized for the source map's box) instead of re-laying them
+    int32_t raw_taps;     // region A is sized for raw boxes: 3-channel tiles staged by TMA or by
+                          // bulk row copies read their taps from the raw rows, not re-laid words
+    int32_t rows16;       // source base and pitch are 16-byte aligned (bulk row copies possible)
     // TMA (per-operation kernels; null in the ragged kernel). Both maps view images as
     // {32-bit word, row, (plane,) image} tensors whose rows are a whole number of words.
     const CUtensorMap *tin;   // source map, box {4 tin_nc words, tin_br rows, 1}; null = cp.async staging
@@ -245,6 +246,16 @@ __device__ __forceinline__ void tma_load_3d(void *sdst, const CUtensorMap *map, 
                  : "memory");
 }
 
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned) from global to
+// shared memory, completing on mbar.
+__device__ __forceinline__ void bulk_load(void *sdst, const void *gsrc, uint32_t bytes, uint64_t *mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_addr(sdst)),
+                 "l"(reinterpret_cast<uint64_t>(gsrc)), "r"(bytes), "r"(smem_addr(mbar))
+                 : "memory");
+}
+
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int c0, int c1, int c2, const void *ssrc)
 {
     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
@@ -404,7 +415,9 @@ struct TileInfo {
 };
 
 template <int TW, int TH> struct TileShared {
-    uint64_t mbar;   // completion barrier of the box's TMA copy
+    uint64_t mbar;         // completion barrier of the box's copies (one phase per staged tile)
+    uint32_t mbar_phase;   // parity of the barrier's next phase
+    int32_t mbar_ok;       // 0 after a wait ran out twice: the barrier is not used again
     TileInfo ti;
     int cx0[TW];     // column tap x0
     int cqd[TW];     // q | (x1 - x0) << 16
@@ -413,6 +426,39 @@ template <int TW, int TH> struct TileShared {
     int rqd[TH];
     float rf[TH];
 };
+
+// Once per CTA, before its first tile (the tile's first barrier publishes it).
+template <int TW, int TH> __device__ __forceinline__ void tile_shared_init(TileShared<TW, TH> &ts)
+{
+    if (threadIdx.x == 0) {
+        mbar_init(&ts.mbar);
+        ts.mbar_phase = 0;
+        ts.mbar_ok = 1;
+    }
+}
+
+// One thread waits (bounded) for the current phase of the staging barrier and records the
+// outcome in ti.tma_ok. A wait that runs out sets error bit 0 and waits once more for the
+// copies to land before the tile is abandoned; if that runs out too the barrier is retired.
+template <int TW, int TH> __device__ __forceinline__ void stage_wait(TileShared<TW, TH> &ts, unsigned *err)
+{
+    const uint32_t ph = ts.mbar_phase;
+    bool ok = mbar_wait_bounded(&ts.mbar, ph, kTmaWaitNs);
+    ts.ti.tma_ok = ok ? 1 : 0;
+    if (!ok) {
+        atomicOr(err, 1u);
+        ok = mbar_wait_bounded(&ts.mbar, ph, kTmaWaitNs);
+    }
+    if (ok) ts.mbar_phase = ph ^ 1u;
+    else ts.mbar_ok = 0;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
 
 // Where one output row of the tile goes in the shared output copy: the HWC row,
 // or the three CHW plane rows (each keeping the 16-byte phase of its global row).
@@ -529,7 +575,10 @@ __device__ __forceinline__ void emit(const Job &J, const ORow &o, int c, uint32_
 // ---------------------------------------------------------------------------
 // The tile engine.
 // ---------------------------------------------------------------------------
-template <int OP, int CIN, int OUTK, int TW, int TH>
+// ROWS: the bulk row-copy staging is compiled in. FRESH: the CTA runs this one tile, and the
+// staging barrier is initialised right before its copies; otherwise the caller ran
+// tile_shared_init once and the barrier's phase carries over from tile to tile.
+template <int OP, int CIN, int OUTK, int TW, int TH, bool ROWS, bool FRESH>
 __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_y, uint8_t *smem,
                                              TileShared<TW, TH> &ts)
 {
@@ -606,12 +655,18 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     const int srow = raw_row_bytes(max(cols, 1), CIN), sw = word_row(max(cols, 1));
     const bool zero_tile = OP == OP_WARP && ti.zero != 0;
     bool staged = !zero_tile && cols >= 1 && rows >= 1 && J.foot_budget > 0;
-    // TMA staging when the launch has a source map whose box holds this tile's box.
-    const bool tma_fits = staged && J.tin != nullptr && rows <= J.tin_br &&
-                          ((fx0 * CIN) & 15) + cols * CIN <= 16 * J.tin_nc;
-    // Raw taps: 3-channel taps are read straight from the TMA-staged rows (region A, which
-    // the launch sized for the map's box), whose 16-byte phase is the same for every row.
-    const bool rawbox = CIN == 3 && J.raw_taps && tma_fits;
+    const int bph = (fx0 * CIN) & 15;   // 16-byte phase of the box in every row of 16-byte aligned rows
+    const bool mbar_ok = FRESH || ts.mbar_ok != 0;
+    // (1) one TMA copy when the launch has a source map whose box holds this tile's box
+    const bool tma_fits = staged && mbar_ok && J.tin != nullptr && rows <= J.tin_br && bph + cols * CIN <= 16 * J.tin_nc;
+    // (2) else one bulk copy per box row when the rows are 16-byte aligned and region A holds
+    // the box (3 channels, raw taps)
+    const int bnc = (bph + cols * CIN + 15) >> 4;   // 16-byte chunks of a box row
+    const bool bulk_fits = ROWS && staged && mbar_ok && !tma_fits && CIN == 3 && J.raw_taps && J.rows16 &&
+                           (long long)rows * 16 * bnc + 16 <= J.foot_budget;
+    // Raw taps: 3-channel taps are read straight from rows staged by (1) or (2) (region A),
+    // whose 16-byte phase is the same for every row.
+    const bool rawbox = CIN == 3 && J.raw_taps && (tma_fits || bulk_fits);
     if (staged && !rawbox) {
         if (CIN == 3)
             staged = (long long)rows * sw * 4 <= J.foot_budget && (long long)rows * srow <= J.region_b;
@@ -620,7 +675,8 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     }
     const bool fast = staged && (OP == OP_RESIZE || ti.fast != 0);   // resize taps always lie in the box
     const bool use_tma = staged && tma_fits;
-    const int rstride = use_tma ? 16 * J.tin_nc : srow;   // bytes between staged raw rows
+    const bool use_bulk = staged && bulk_fits;
+    const int rstride = use_tma ? 16 * J.tin_nc : use_bulk ? 16 * bnc : srow;   // bytes between staged raw rows
     uint8_t *regA = smem;
     uint8_t *regB = smem + J.foot_budget;
     uint8_t *raw = (CIN == 3 && !rawbox) ? regB : regA;
@@ -643,13 +699,61 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             // outside the image (left of it, right of its last word, above, below) arrive as
             // zeros: the zero border of warp boxes.
             if (tid == 0) {
-                mbar_init(&ts.mbar);
+                if (FRESH) tile_shared_init(ts);
                 mbar_expect_tx(&ts.mbar, (uint32_t)(16 * J.tin_nc * J.tin_br));
                 tma_load_3d(raw, J.tin, 4 * ((fx0 * CIN) >> 4), fy0, J.zimg, &ts.mbar);
-                ti.tma_ok = mbar_wait_bounded(&ts.mbar, 0, kTmaWaitNs) ? 1 : 0;
-                if (!ti.tma_ok) {
-                    atomicOr(J.err, 1u);
-                    mbar_wait_bounded(&ts.mbar, 0, kTmaWaitNs);   // let the copy land before leaving
+                stage_wait(ts, J.err);
+            }
+            __syncthreads();
+            if (!ti.tma_ok) return;
+        } else if (use_bulk) {
+            // Box row r is the row's bytes [xb0, xb1) (16-byte chunks from the one holding byte
+            // fx0*3). Warp 0 copies each row's whole chunks inside the image, [0, F), with one
+            // bulk copy; the other warps write what the copies do not cover: zeros outside the
+            // image (the warp's zero border; resize never reads there) and the bytes of a row's
+            // last partial chunk [F, 3W), byte by byte.
+            const int xb0 = 16 * ((fx0 * CIN) >> 4), xb1 = xb0 + 16 * bnc;
+            const int F = (J.W * CIN) & ~15;
+            const int c0 = max(xb0, 0), c1 = min(xb1, F);   // copied byte range of an image row
+            if (warp == 0) {
+                uint32_t bytes = 0;
+                if (c1 > c0)
+                    for (int r = lane; r < rows; r += 32)
+                        if ((unsigned)(fy0 + r) < (unsigned)J.H) bytes += (uint32_t)(c1 - c0);
+                bytes = warp_sum(bytes);
+                if (lane == 0) {
+                    if (FRESH) tile_shared_init(ts);
+                    mbar_expect_tx(&ts.mbar, bytes);
+                }
+                __syncwarp();
+                if (c1 > c0)
+                    for (int r = lane; r < rows; r += 32) {
+                        const int y = fy0 + r;
+                        if ((unsigned)y < (unsigned)J.H)
+                            bulk_load(raw + r * rstride + (c0 - xb0), J.src + (int64_t)y * J.spitch + c0,
+                                      (uint32_t)(c1 - c0), &ts.mbar);
+                    }
+                if (lane == 0) stage_wait(ts, J.err);
+            } else if (!(fy0 >= 0 && fy1 < J.H && xb0 >= 0 && xb1 <= F)) {
+                const int L3 = J.W * CIN;
+                for (int r = warp - 1; r < rows; r += kWarps - 1) {
+                    const int y = fy0 + r;
+                    const bool yin = (unsigned)y < (unsigned)J.H;
+                    const uint8_t *grow = J.src + (int64_t)y * J.spitch;
+                    uint8_t *srow_p = raw + r * rstride;
+                    for (int j = lane; j < bnc; j += 32) {
+                        const int b0 = xb0 + 16 * j;
+                        if (yin && b0 >= c0 && b0 + 16 <= c1) continue;   // copied
+                        uint8_t *d = srow_p + 16 * j;
+                        if (!yin || b0 + 16 <= 0 || b0 >= L3) {
+                            *reinterpret_cast<uint4 *>(d) = make_uint4(0u, 0u, 0u, 0u);
+                        } else {
+                            for (int k = 0; k < 16; ++k) {
+                                const int b = b0 + k;
+                                d[k] = (b >= 0 && b < L3) ? __ldg(grow + b) : (uint8_t)0;
+                            }
+                        }
+                    }
                 }
             }
             __syncthreads();
@@ -726,9 +830,9 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     constexpr int BH = out_band_rows<OUTK, CIN, TH>();
     constexpr int NBAND = TH / BH;
     const bool chw = OT::is_f32 && dC == 3 && J.chw;
+    const int rph = (fx0 * CIN) & 15;   // phase of every raw-staged row (raw taps)
     // output rows: dense when the tile leaves through a TMA store (its rows are 16-byte
     // aligned), else with room for each row's 16-byte phase
-    const int rph = (fx0 * CIN) & 15;   // phase of every TMA-staged row (raw taps)
     const bool tma_out = J.tout != nullptr;
     const int orow = tma_out ? (chw ? TW * 4 : TW * dC * ES) : (chw ? round16(TW * 4 + 15) : round16(TW * dC * ES + 15));
     // low address bits of output row 0 of the tile (plane 0): staging rows keep their phase

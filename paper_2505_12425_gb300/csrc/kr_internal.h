@@ -50,6 +50,8 @@ cudaError_t launch_gray(const GrayDesc &d, cudaStream_t stream);
 
 // Shared-memory budget of one tile: region A bytes (0 = no staging) and region B bytes
 // (at least out_bytes, the output tile). Multiples of 16.
+inline int round128(int x) { return (x + 127) & ~127; }
+
 struct Budget {
     int a = 0;
     int b = 0;
@@ -65,6 +67,7 @@ bool warp_allows_fast(const float *M, int h, int w);
 
 // Device error flags of the per-operation kernels (synchronous read, optional clear).
 cudaError_t device_error_flags(unsigned *flags, bool clear);
+cudaError_t batch_error_flags(unsigned *flags, bool clear);
 
 // Validation + descriptor construction (kr_abi.cu); nothing is enqueued.
 kr_status build_resample(int op, const kr_image_t *src, const kr_image_t *dst, const kr_post_t *post,

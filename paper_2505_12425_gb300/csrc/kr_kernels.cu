@@ -35,12 +35,15 @@ struct OpParams {
     int32_t foot_budget;
     int32_t region_b;
     int32_t raw_taps;
+    int32_t rows16;
     uint32_t fast_mask[(kMaxMPerLaunch + 31) / 32];   // warp: images whose map allows the fast path
     float scale[3], bias[3];
     float M[kMaxMPerLaunch][6];
 };
 
-template <int OP, int CIN, int OUTK, int TW, int TH>
+// ROWS: instantiated for launches whose 3-channel boxes are staged by bulk row copies (no
+// tensor map, 16-byte aligned rows); the others do without that code.
+template <int OP, int CIN, int OUTK, int TW, int TH, bool ROWS>
 __global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constant__ OpParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -60,6 +63,7 @@ __global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constan
     J.foot_budget = p.foot_budget;
     J.region_b = p.region_b;
     J.raw_taps = p.raw_taps;
+    J.rows16 = p.rows16;
     J.allow_fast = OP == OP_WARP ? (int)((p.fast_mask[z >> 5] >> (z & 31)) & 1u) : 1;
     J.tin = p.has_tin ? &p.tin : nullptr;
     J.tin_nc = p.tin_nc;
@@ -74,13 +78,12 @@ __global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constan
         J.scale[k] = p.scale[k];
         J.bias[k] = p.bias[k];
     }
-    process_tile<OP, CIN, OUTK, TW, TH>(J, blockIdx.x, blockIdx.y, smem, ts);
+    process_tile<OP, CIN, OUTK, TW, TH, ROWS, true>(J, blockIdx.x, blockIdx.y, smem, ts);
 }
 
 // ---------------------------------------------------------------------------
 // Shared-memory budgets
 // ---------------------------------------------------------------------------
-static int round128(int x) { return (x + 127) & ~127; }
 
 // clamp: boxes larger than the caps are staged when they fit (warp); else never staged.
 // Resize boxes lie inside the image (clipped to W x H); warp boxes are not clipped.
@@ -201,13 +204,16 @@ template <int OP, int CIN, int OUTK>
 static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
 {
     constexpr int TW = kTW, TH = kTH;
-    auto kern = resample_kernel<OP, CIN, OUTK, TW, TH>;
+    auto kern_map = resample_kernel<OP, CIN, OUTK, TW, TH, false>;
+    auto kern_rows = resample_kernel<OP, CIN, OUTK, TW, TH, CIN == 3>;
     static unsigned attr_done = 0;   // one bit per device ordinal (< 32)
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 32 || !(attr_done & (1u << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kFootCap + std::max(kRegionBCap, out_stage_bytes<OUTK, CIN, TW, TH>()));
+        const int max_smem = kFootCap + std::max(kRegionBCap, out_stage_bytes<OUTK, CIN, TW, TH>());
+        cudaError_t e = cudaFuncSetAttribute(kern_map, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(kern_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e != cudaSuccess) return e;
         if (dev < 32) __atomic_fetch_or(&attr_done, 1u << dev, __ATOMIC_RELAXED);
     }
@@ -258,6 +264,7 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
         // TMA source map: one box per tile covering the largest source box of the launch
         p.has_tin = 0;
         p.raw_taps = 0;
+        p.rows16 = ((uintptr_t)p.src & 15) == 0 && (d.spitch & 15) == 0 && (nb == 1 || (d.sbatch & 15) == 0);
         if (bud.a > 0 && bud.cols > 0 && bud.rows > 0) {
             const int nc = (15 + bud.cols * CIN + 15) / 16, br = bud.rows;
             const long long cap = CIN == 3 ? bud.b : bud.a - 16;
@@ -276,6 +283,17 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
                 }
             }
         }
+        if (CIN == 3 && !p.has_tin && p.rows16 && bud.a > 0 && bud.cols > 0 && bud.rows > 0) {
+            // no map, but 16-byte aligned rows: bulk row copies and raw taps, region A sized
+            // for the largest box (plus the 16 bytes a last pixel pair may touch)
+            const int nc = (15 + bud.cols * CIN + 15) / 16;
+            const long long a = 16LL * nc * bud.rows + 16;
+            if (a <= std::max<long long>(bud.b, kRegionBCap)) {
+                p.raw_taps = 1;
+                bud.a = round128((int)a);
+                bud.b = round16(ob);
+            }
+        }
         p.foot_budget = bud.a;
         p.region_b = bud.b;
         // TMA destination map: one band of a tile, when every row is a whole number of 16-byte chunks
@@ -290,7 +308,10 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
         }
         const size_t smem = (size_t)bud.a + bud.b;
         dim3 grid(tiles_x, tiles_y, nb);
-        kern<<<grid, kThreads, smem, stream>>>(p);
+        if (p.raw_taps && !p.has_tin)
+            kern_rows<<<grid, kThreads, smem, stream>>>(p);
+        else
+            kern_map<<<grid, kThreads, smem, stream>>>(p);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

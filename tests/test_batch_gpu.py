@@ -110,8 +110,22 @@ def as_hwc(t, layout):
     return a.transpose(1, 2, 0) if layout == "chw" else a
 
 
-def run_batch(items, tile_config=-1, use_graph=False, ctas=0):
-    srcs = [torch.from_numpy(it["img"]).to(dev()) for it in items]
+def to_src(img, pitched):
+    """The image on the device: contiguous, or inside rows of a 64-byte multiple pitch whose
+    padding holds 0xC3 (16-byte aligned rows: staged by bulk row copies)."""
+    t = torch.from_numpy(img).to(dev())
+    if not pitched:
+        return t
+    H, W, C = img.shape
+    pitch = (W * C + 63) // 64 * 64
+    buf = torch.full((H * pitch,), 0xC3, dtype=torch.uint8, device=dev())
+    v = torch.as_strided(buf, (H, W, C), (pitch, C, 1))
+    v.copy_(t)
+    return v
+
+
+def run_batch(items, tile_config=-1, use_graph=False, ctas=0, pitched=False):
+    srcs = [to_src(it["img"], pitched) for it in items]
     dsts = [alloc_dst(it) for it in items]
     work = kr.work_array([work_of(it, s, d, l) for it, s, (d, l) in zip(items, srcs, dsts)])
     ws = torch.empty(kr.kr_batch_workspace_size(len(items)), dtype=torch.uint8, device=dev())
@@ -122,9 +136,10 @@ def run_batch(items, tile_config=-1, use_graph=False, ctas=0):
     return srcs, dsts
 
 
-def test_mixed_batch_matches_oracle_and_single_calls():
+@pytest.mark.parametrize("pitched", [False, True])
+def test_mixed_batch_matches_oracle_and_single_calls(pitched):
     items = make_mixed(1, 40)
-    srcs, dsts = run_batch(items)
+    srcs, dsts = run_batch(items, pitched=pitched)
     for it, s, (d, l) in zip(items, srcs, dsts):
         ref = oracle_of(it)
         got = as_hwc(d, l)
@@ -138,13 +153,14 @@ def test_mixed_batch_matches_oracle_and_single_calls():
         assert torch.equal(single, d), (it["op"], it["kind"])
 
 
+@pytest.mark.parametrize("pitched", [False, True])
 @pytest.mark.parametrize("use_graph", [False, True])
-def test_every_tile_config(use_graph):
+def test_every_tile_config(use_graph, pitched):
     items = make_mixed(2, 20)
     ref = None
     for cfg in range(kr.kr_tile_config_count()):
         for _ in range(2):      # second pass replays the graph
-            _, dsts = run_batch(items, tile_config=cfg, use_graph=use_graph)
+            _, dsts = run_batch(items, tile_config=cfg, use_graph=use_graph, pitched=pitched)
         outs = [d.cpu() for d, _ in dsts]
         if ref is None:
             ref = outs
@@ -209,14 +225,15 @@ def test_workspace_too_small_is_rejected():
     assert e.value.status == 5
 
 
-def test_ragged_256_warps_full_size():
+@pytest.mark.parametrize("pitched", [False, True])
+def test_ragged_256_warps_full_size(pitched):
     """256 warps, sides log-uniform 64..2048, output scale 0.25-2x: the batch equals
     256 single-image launches everywhere and the oracle on sampled items."""
     spec = inputs.ragged_batch(1003, 256)
     srcs, dsts, work = [], [], []
     for it in spec:
         img = inputs.uniform_image(it.seed, it.H, it.W, 3)
-        s = torch.from_numpy(img).to(dev())
+        s = to_src(img, pitched)
         d = torch.empty((it.h, it.w, 3), dtype=torch.uint8, device=dev())
         srcs.append(s)
         dsts.append(d)

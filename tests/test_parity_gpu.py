@@ -255,12 +255,13 @@ def test_views_with_odd_pitch_and_offset():
         assert bool((b[m] == CANARY_U8).all()), "write outside the destination view"
 
 
-def test_tma_staging_of_padded_views():
-    # Rows of 100 pixels (300 bytes, a whole number of words) inside rows of 112 (336
-    # bytes, a multiple of 16) that start 16-byte aligned: the source is staged by TMA. The
-    # row padding (set to 200 here) must never be read: right of each row the copy engine
-    # fills zeros, the zero border of warp boxes.
-    n, H, Wp, W = 3, 150, 112, 100
+@pytest.mark.parametrize("W", [100, 101])
+def test_tma_staging_of_padded_views(W):
+    # Rows of W pixels inside rows of 112 (336 bytes, a multiple of 16) that start 16-byte
+    # aligned. W = 100 (300 bytes, a whole number of words): the source is staged by TMA;
+    # W = 101 (303 bytes): by bulk row copies. The row padding (set to 200 here) must never
+    # be read: right of each row the staged box holds zeros, the zero border of warp boxes.
+    n, H, Wp = 3, 150, 112
     imgs = np.stack([inputs.noise_gradient_image(60 + i, H, W) for i in range(n)])
     big = torch.full((n, H, Wp, 3), 200, dtype=torch.uint8, device=dev())
     big[:, :, :W] = to_dev(imgs)
