@@ -204,13 +204,24 @@ class Step:
                 events[i][1].record()
 
 
+def pitched(torch, img, dev, align=64):
+    """A device copy of an HWC u8 image whose rows start `align`-byte aligned (pitched, as a
+    resident image pool lays frames out in HBM; the row padding is never read)."""
+    H, W, C = img.shape
+    pitch = (W * C + align - 1) // align * align
+    buf = torch.empty((H * pitch,), dtype=torch.uint8, device=dev)
+    v = torch.as_strided(buf, (H, W, C), (pitch, C, 1))
+    v.copy_(torch.from_numpy(img).to(dev))
+    return v
+
+
 def ragged_compare(torch, kr, dev, reps=20):
-    """256 warps (sides log-uniform 64..2048, output 0.25-2x): one persistent graph-replayed
-    launch vs 256 per-image launches. Returns a summary dict."""
+    """256 warps (sides log-uniform 64..2048, output 0.25-2x, pitched sources): one persistent
+    graph-replayed launch vs 256 per-image launches. Returns a summary dict."""
     spec = inputs.ragged_batch(1003, 256)
     srcs, dsts, work = [], [], []
     for it in spec:
-        s = torch.from_numpy(inputs.uniform_image(it.seed, it.H, it.W, 3)).to(dev)
+        s = pitched(torch, inputs.uniform_image(it.seed, it.H, it.W, 3), dev)
         d = torch.empty((it.h, it.w, 3), dtype=torch.uint8, device=dev)
         srcs.append(s)
         dsts.append(d)
@@ -263,10 +274,10 @@ def ragged_compare(torch, kr, dev, reps=20):
 def serving_compare(torch, kr, dev, rates=(2000, 5000, 10000, 20000, 40000, 80000, 160000, 320000, 640000),
                     seconds=1.0):
     """Poisson request streams (sizes log-uniform 320..3840 x 240..2160, op uniform over
-    resize / warp / gray) over a device-resident pool of 64 images, 8 GB in-flight budget:
+    resize / warp / gray) over a device-resident pool of 64 pitched images, 8 GB in-flight budget:
     continuous batching (policy 0) vs one launch per request (policy 1)."""
     sizes = inputs.pool_sizes(1004, 64)
-    pool = [torch.from_numpy(inputs.uniform_image(5000 + i, H, W, 3)).to(dev) for i, (H, W) in enumerate(sizes)]
+    pool = [pitched(torch, inputs.uniform_image(5000 + i, H, W, 3), dev) for i, (H, W) in enumerate(sizes)]
     arena = torch.empty(8 << 30, dtype=torch.uint8, device=dev)
     out = {"pool_images": 64, "budget_bytes": 8 << 30, "seconds_per_rate": seconds, "streams": 4,
            "max_batch": 64, "runs": []}

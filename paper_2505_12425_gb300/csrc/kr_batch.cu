@@ -1,17 +1,20 @@
 // Ragged batches: many independent resize / warp / gray items of different
-// sizes, matrices and output sizes in ONE persistent launch.
+// sizes, matrices and output sizes in one submission.
 //
-//   host:   validate every item -> pack a work list {header, items, tile prefix}
-//           into a pinned staging slot -> one async H2D copy into the caller's
-//           workspace -> one persistent kernel (optionally both replayed from a
-//           CUDA graph);
-//   device: #SM x k CTAs pull tile indices from an atomic counter in the
-//           workspace header, find the owning item by binary search over the
-//           tile prefix, and run the same tile engine as the single-image
-//           kernels for that item's (op, channels, output kind).
+//   host:   validate every item -> pack a work list {header, items grouped by
+//           kind (op, channels, output kind), tile prefix} into a pinned staging
+//           slot -> one async H2D copy into the caller's workspace -> one
+//           persistent kernel per kind present, specialised for that kind, the
+//           launches overlapping (programmatic dependent launch on a stream,
+//           parallel branches in a CUDA graph);
+//   device: #SM x k CTAs of each kernel pull tile indices of their kind from an
+//           atomic counter in the workspace header, find the owning item by
+//           binary search over the tile prefix, and run the same tile engine as
+//           the single-image kernels.
 //
-// The tile shape (and CTAs per SM) comes from a small autotuner that times
-// every configuration on the batch and caches the winner per batch class.
+// The tile shape and CTAs per SM (which sets the shared-memory cap of the
+// launch) come from a small autotuner that times the candidates on the batch
+// and caches the winner per batch class.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -46,16 +49,34 @@ struct alignas(16) WorkItem {
 };
 static_assert(sizeof(WorkItem) == 128, "work item is 128 bytes");
 
-struct alignas(16) WsHeader {
-    unsigned next;         // tile counter (0 in every freshly copied header)
-    int n;                 // items
-    int total_tiles;
-    int pad[61];
-};
-static_assert(sizeof(WsHeader) == 256, "header is 256 bytes");
-
 constexpr int kind_of(int op, int cin, int outk) { return op | (cin << 4) | (outk << 8); }
 constexpr int KIND_GRAY = 0x1000;
+// The kinds of work item, one specialised kernel (and one group of the work list) each.
+constexpr int kGroups = 13;
+constexpr int kKinds[kGroups] = {
+    kind_of(OP_RESIZE, 3, OUT_U8), kind_of(OP_RESIZE, 3, OUT_U8_GRAY), kind_of(OP_RESIZE, 3, OUT_F32),
+    kind_of(OP_RESIZE, 3, OUT_F32_GRAY), kind_of(OP_RESIZE, 1, OUT_U8), kind_of(OP_RESIZE, 1, OUT_F32),
+    kind_of(OP_WARP, 3, OUT_U8), kind_of(OP_WARP, 3, OUT_U8_GRAY), kind_of(OP_WARP, 3, OUT_F32),
+    kind_of(OP_WARP, 3, OUT_F32_GRAY), kind_of(OP_WARP, 1, OUT_U8), kind_of(OP_WARP, 1, OUT_F32), KIND_GRAY};
+static int group_of(int kind)
+{
+    for (int g = 0; g < kGroups; ++g)
+        if (kKinds[g] == kind) return g;
+    return -1;
+}
+
+struct alignas(16) WsHeader {
+    unsigned next[16];        // per-group tile counters (0 in every freshly copied header)
+    int n;                    // items
+    int total_tiles;
+    int pad0[2];
+    int first_item[16];       // group g: items [first_item[g], first_item[g] + items[g])
+    int items[16];
+    int first_tile[16];       // group g: tiles [first_tile[g], first_tile[g] + tiles[g])
+    int tiles[16];
+    int pad1[44];
+};
+static_assert(sizeof(WsHeader) == 512, "header is 512 bytes");
 // item flags: the warp map allows the fast path; region A is sized for raw boxes; the
 // source rows are 16-byte aligned (bulk row copies)
 constexpr int ITEM_FAST = 1, ITEM_RAW = 2, ITEM_ROWS16 = 4;
@@ -115,23 +136,33 @@ __device__ __forceinline__ Job job_of(const WorkItem &it)
     return J;
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(kThreads) ragged_kernel(uint8_t *ws)
+// Register budgets: f32 kinds 64 (4 CTAs per SM), the others 48 (5).
+constexpr bool kind_is_f32(int kind) { return kind != KIND_GRAY && ((kind >> 8) & 15) >= OUT_F32; }
+
+template <int TW, int TH, int G>
+__global__ void __launch_bounds__(kThreads, kind_is_f32(kKinds[G]) ? 4 : 5) ragged_kernel(uint8_t *ws)
 {
+    // The next kind's kernel in the stream may start now: the kinds share no data.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    constexpr int KIND = kKinds[G];
+    constexpr int OP = KIND & 15, CIN = (KIND >> 4) & 15, OUTK = (KIND >> 8) & 15;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ TileShared<TW, TH> ts;
     __shared__ int s_tile;
     WsHeader *hdr = reinterpret_cast<WsHeader *>(ws);
     const WorkItem *items = reinterpret_cast<const WorkItem *>(ws + sizeof(WsHeader));
-    const int n = hdr->n, total = hdr->total_tiles;
+    const int n = hdr->n;
     const int *prefix = reinterpret_cast<const int *>(items + n);
-    tile_shared_init(ts);
+    const int i0 = hdr->first_item[G], i1 = i0 + hdr->items[G] - 1;
+    const int t0 = hdr->first_tile[G], tiles = hdr->tiles[G];
+    if (KIND != KIND_GRAY) tile_shared_init(ts);
     for (;;) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&hdr->next, 1u);
+        if (threadIdx.x == 0) s_tile = (int)atomicAdd(&hdr->next[G], 1u);
         __syncthreads();
-        const int t = s_tile;
-        if (t >= total) break;
-        int lo = 0, hi = n - 1;   // last item whose first tile is <= t
+        const int tl = s_tile;
+        if (tl >= tiles) break;
+        const int t = t0 + tl;
+        int lo = i0, hi = i1;   // last item of the group whose first tile is <= t
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (__ldg(prefix + mid) <= t) lo = mid; else hi = mid - 1;
@@ -139,33 +170,15 @@ __global__ void __launch_bounds__(kThreads) ragged_kernel(uint8_t *ws)
         const WorkItem &it = items[lo];
         const int local = t - __ldg(prefix + lo);
         const int ty = local / it.tiles_x, tx = local - ty * it.tiles_x;
-        if (it.kind == KIND_GRAY) {
+        if (KIND == KIND_GRAY) {
             gray_tile<TW, TH>(it, tx, ty);
         } else {
-            const Job J = job_of(it);
-            switch (it.kind) {
-#define KR_CASE(OP, CIN, OUTK) \
-    case kind_of(OP, CIN, OUTK): process_tile<OP, CIN, OUTK, TW, TH, true, false>(J, tx, ty, smem, ts); break;
-            KR_CASE(OP_RESIZE, 3, OUT_U8)
-            KR_CASE(OP_RESIZE, 3, OUT_U8_GRAY)
-            KR_CASE(OP_RESIZE, 3, OUT_F32)
-            KR_CASE(OP_RESIZE, 3, OUT_F32_GRAY)
-            KR_CASE(OP_RESIZE, 1, OUT_U8)
-            KR_CASE(OP_RESIZE, 1, OUT_F32)
-            KR_CASE(OP_WARP, 3, OUT_U8)
-            KR_CASE(OP_WARP, 3, OUT_U8_GRAY)
-            KR_CASE(OP_WARP, 3, OUT_F32)
-            KR_CASE(OP_WARP, 3, OUT_F32_GRAY)
-            KR_CASE(OP_WARP, 1, OUT_U8)
-            KR_CASE(OP_WARP, 1, OUT_F32)
-#undef KR_CASE
-            default: break;
-            }
+            process_tile<OP, CIN, OUTK, TW, TH, true, false>(job_of(it), tx, ty, smem, ts);
         }
         __syncthreads();   // everyone has read s_tile before thread 0 rewrites it
         // a staging wait ran out twice: copies may still be in flight into this CTA's shared
         // memory, so it takes no further tiles (the others finish the list; error bit set)
-        if (!ts.mbar_ok) break;
+        if (KIND != KIND_GRAY && !ts.mbar_ok) break;
     }
 }
 
@@ -184,7 +197,7 @@ cudaError_t batch_error_flags(unsigned *flags, bool clear)
 // ---------------------------------------------------------------------------
 struct TileCfg {
     int tw, th;
-    const void *kernel;
+    const void *kernels[kGroups];
     int max_smem;
 };
 
@@ -193,12 +206,21 @@ template <int TW, int TH> static constexpr int max_region_b()
     return 3 * (TH / 2) * round16(TW * 4 + 15) > kRegionBCap ? 3 * (TH / 2) * round16(TW * 4 + 15) : kRegionBCap;
 }
 
+#define KR_KERNELS(TW, TH)                                                                                     \
+    {(const void *)ragged_kernel<TW, TH, 0>, (const void *)ragged_kernel<TW, TH, 1>,                            \
+     (const void *)ragged_kernel<TW, TH, 2>, (const void *)ragged_kernel<TW, TH, 3>,                            \
+     (const void *)ragged_kernel<TW, TH, 4>, (const void *)ragged_kernel<TW, TH, 5>,                            \
+     (const void *)ragged_kernel<TW, TH, 6>, (const void *)ragged_kernel<TW, TH, 7>,                            \
+     (const void *)ragged_kernel<TW, TH, 8>, (const void *)ragged_kernel<TW, TH, 9>,                            \
+     (const void *)ragged_kernel<TW, TH, 10>, (const void *)ragged_kernel<TW, TH, 11>,                          \
+     (const void *)ragged_kernel<TW, TH, 12>}
 static TileCfg g_cfgs[] = {
-    {64, 32, (const void *)ragged_kernel<64, 32>, kFootCap + max_region_b<64, 32>()},
-    {32, 32, (const void *)ragged_kernel<32, 32>, kFootCap + max_region_b<32, 32>()},
-    {128, 16, (const void *)ragged_kernel<128, 16>, kFootCap + max_region_b<128, 16>()},
-    {64, 16, (const void *)ragged_kernel<64, 16>, kFootCap + max_region_b<64, 16>()},
+    {64, 32, KR_KERNELS(64, 32), kFootCap + max_region_b<64, 32>()},
+    {32, 32, KR_KERNELS(32, 32), kFootCap + max_region_b<32, 32>()},
+    {128, 16, KR_KERNELS(128, 16), kFootCap + max_region_b<128, 16>()},
+    {64, 16, KR_KERNELS(64, 16), kFootCap + max_region_b<64, 16>()},
 };
+#undef KR_KERNELS
 constexpr int kNumCfgs = sizeof(g_cfgs) / sizeof(g_cfgs[0]);
 
 // The output stage of process_tile (out_stage_bytes) for a runtime kind: f32 tiles stage
@@ -215,72 +237,121 @@ static int out_stage_of(int outk, int cin, int tw, int th)
 // ---------------------------------------------------------------------------
 struct PackInfo {
     int total_tiles = 0;
-    size_t smem = 0;        // dynamic shared bytes the launch needs
+    size_t smem = 0;        // dynamic shared bytes of the largest group launch
     int opmask = 0;
     double out_px = 0;
+    // per kind group (items are stored group by group)
+    int first_item[kGroups] = {}, items[kGroups] = {};
+    int first_tile[kGroups] = {}, tiles[kGroups] = {};
+    size_t gsmem[kGroups] = {};   // dynamic shared bytes the group's launch needs
 };
 
+// Validate one item and write it as a device work item for tile shape (tw, th); smem gets
+// the dynamic shared bytes it needs (see pack_into for smem_cap).
+static kr_status build_item(const kr_work_t &w, int tw, int th, int smem_cap, WorkItem &it, size_t &smem)
+{
+    if (w.src.batch != 1 || w.dst.batch != 1) return KR_ERR_INVALID_ARG;
+    std::memset(&it, 0, sizeof(it));
+    smem = 0;
+    if (w.op == KR_OP_GRAY) {
+        GrayDesc g;
+        kr_status st = build_gray(&w.src, &w.dst, g);
+        if (st != KR_OK) return st;
+        it.src = g.src; it.dst = g.dst; it.spitch = g.spitch; it.dpitch = g.dpitch;
+        it.H = it.h = g.H; it.W = it.w = g.W;
+        it.kind = KIND_GRAY;
+    } else if (w.op == KR_OP_RESIZE || w.op == KR_OP_WARP) {
+        const int op = w.op == KR_OP_RESIZE ? OP_RESIZE : OP_WARP;
+        OpDesc d;
+        kr_status st = build_resample(op, &w.src, &w.dst, &w.post, d);
+        if (st != KR_OK) return st;
+        if (op == OP_WARP)
+            for (int k = 0; k < 6; ++k)
+                if (!std::isfinite(w.M[k])) return KR_ERR_INVALID_ARG;
+        it.src = d.src; it.dst = d.dst; it.spitch = d.spitch; it.dpitch = d.dpitch;
+        it.dplane = d.dplane; it.H = d.H; it.W = d.W; it.h = d.h; it.w = d.w; it.chw = d.chw;
+        it.kind = kind_of(op, d.cin, d.outk);
+        for (int k = 0; k < 6; ++k) it.M[k] = op == OP_WARP ? w.M[k] : 0.f;
+        for (int k = 0; k < 3; ++k) { it.scale[k] = d.scale[k]; it.bias[k] = d.bias[k]; }
+        const int ob = out_stage_of(d.outk, d.cin, tw, th);
+        Budget bud = op == OP_RESIZE ? budget_resize(d.cin, d.H, d.W, d.h, d.w, tw, th, ob)
+                                     : budget_warp(d.cin, d.H, d.W, it.M, tw, th, ob);
+        it.flags = (op == OP_RESIZE || warp_allows_fast(it.M, d.h, d.w)) ? ITEM_FAST : 0;
+        const bool rows16 = ((uintptr_t)d.src & 15) == 0 && (d.spitch & 15) == 0;
+        if (rows16) it.flags |= ITEM_ROWS16;
+        if (d.cin == 3 && rows16 && bud.a > 0 && bud.fits) {
+            // bulk row copies and raw taps: region A holds the item's largest box (plus
+            // the 16 bytes a last pixel pair may touch), region B only the output tile
+            const long long a = 16LL * ((15 + bud.cols * 3 + 15) / 16) * bud.rows + 16;
+            if (a <= std::max<long long>(bud.b, kRegionBCap)) {
+                it.flags |= ITEM_RAW;
+                bud.a = round128((int)a);
+                bud.b = round16(ob);
+            }
+        }
+        if ((long long)bud.a + bud.b > smem_cap) {
+            const int b_min = round16(ob);
+            if (b_min > smem_cap) return KR_ERR_NO_SPACE;   // not even the output stage fits
+            if (it.flags & ITEM_RAW) {
+                bud.b = b_min;
+                bud.a = (smem_cap - b_min) & ~127;
+            } else {
+                bud.a = 0;   // re-laid staging needs both regions: take the unstaged path
+                bud.b = b_min;
+            }
+        }
+        it.foot_budget = bud.a;
+        it.region_b = bud.b;
+        smem = (size_t)bud.a + bud.b;
+    } else {
+        return KR_ERR_INVALID_ARG;
+    }
+    it.tiles_x = (it.w + tw - 1) / tw;
+    return KR_OK;
+}
+
 // Validate all items and write them as device work items for tile shape (tw, th) into
-// out[0..n) and their first-tile indices into prefix[0..n]. Allocates nothing.
-static kr_status pack_into(const kr_work_t *items, int n, int tw, int th, WorkItem *out, int *prefix,
-                           PackInfo &P)
+// out[0..n), grouped by kind (group g in out[first_item[g] ..]), and their first-tile
+// indices into prefix[0..n]. Allocates nothing. smem_cap bounds the dynamic shared memory
+// of every launch (the residency the caller wants): an item whose boxes need more stages
+// only the tiles whose box fits what is left next to its output stage, and its other tiles
+// read their taps from global memory.
+static kr_status pack_into(const kr_work_t *items, int n, int tw, int th, int smem_cap, WorkItem *out,
+                           int *prefix, PackInfo &P)
 {
     P = PackInfo();
-    long long total = 0;
+    // pass 1: validate, count the items of each kind
     for (int i = 0; i < n; ++i) {
-        const kr_work_t &w = items[i];
-        if (w.src.batch != 1 || w.dst.batch != 1) return KR_ERR_INVALID_ARG;
-        WorkItem &it = out[i];
-        std::memset(&it, 0, sizeof(it));
-        if (w.op == KR_OP_GRAY) {
-            GrayDesc g;
-            kr_status st = build_gray(&w.src, &w.dst, g);
-            if (st != KR_OK) return st;
-            it.src = g.src; it.dst = g.dst; it.spitch = g.spitch; it.dpitch = g.dpitch;
-            it.H = it.h = g.H; it.W = it.w = g.W;
-            it.kind = KIND_GRAY;
-        } else if (w.op == KR_OP_RESIZE || w.op == KR_OP_WARP) {
-            const int op = w.op == KR_OP_RESIZE ? OP_RESIZE : OP_WARP;
-            OpDesc d;
-            kr_status st = build_resample(op, &w.src, &w.dst, &w.post, d);
-            if (st != KR_OK) return st;
-            if (op == OP_WARP)
-                for (int k = 0; k < 6; ++k)
-                    if (!std::isfinite(w.M[k])) return KR_ERR_INVALID_ARG;
-            it.src = d.src; it.dst = d.dst; it.spitch = d.spitch; it.dpitch = d.dpitch;
-            it.dplane = d.dplane; it.H = d.H; it.W = d.W; it.h = d.h; it.w = d.w; it.chw = d.chw;
-            it.kind = kind_of(op, d.cin, d.outk);
-            for (int k = 0; k < 6; ++k) it.M[k] = op == OP_WARP ? w.M[k] : 0.f;
-            for (int k = 0; k < 3; ++k) { it.scale[k] = d.scale[k]; it.bias[k] = d.bias[k]; }
-            const int ob = out_stage_of(d.outk, d.cin, tw, th);
-            Budget bud = op == OP_RESIZE ? budget_resize(d.cin, d.H, d.W, d.h, d.w, tw, th, ob)
-                                         : budget_warp(d.cin, d.H, d.W, it.M, tw, th, ob);
-            it.flags = (op == OP_RESIZE || warp_allows_fast(it.M, d.h, d.w)) ? ITEM_FAST : 0;
-            const bool rows16 = ((uintptr_t)d.src & 15) == 0 && (d.spitch & 15) == 0;
-            if (rows16) it.flags |= ITEM_ROWS16;
-            if (d.cin == 3 && rows16 && bud.a > 0 && bud.fits) {
-                // bulk row copies and raw taps: region A holds the item's largest box (plus
-                // the 16 bytes a last pixel pair may touch), region B only the output tile
-                const long long a = 16LL * ((15 + bud.cols * 3 + 15) / 16) * bud.rows + 16;
-                if (a <= std::max<long long>(bud.b, kRegionBCap)) {
-                    it.flags |= ITEM_RAW;
-                    bud.a = round128((int)a);
-                    bud.b = round16(ob);
-                }
-            }
-            it.foot_budget = bud.a;
-            it.region_b = bud.b;
-            P.smem = std::max(P.smem, (size_t)bud.a + bud.b);
-        } else {
-            return KR_ERR_INVALID_ARG;
-        }
-        P.opmask |= 1 << w.op;
+        WorkItem it;
+        size_t sm;
+        kr_status st = build_item(items[i], tw, th, smem_cap, it, sm);
+        if (st != KR_OK) return st;
+        P.items[group_of(it.kind)]++;
+    }
+    for (int g = 1; g < kGroups; ++g) P.first_item[g] = P.first_item[g - 1] + P.items[g - 1];
+    // pass 2: each item into the next slot of its group
+    int fill[kGroups] = {};
+    for (int i = 0; i < n; ++i) {
+        WorkItem it;
+        size_t sm;
+        kr_status st = build_item(items[i], tw, th, smem_cap, it, sm);
+        if (st != KR_OK) return st;
+        const int g = group_of(it.kind);
+        out[P.first_item[g] + fill[g]++] = it;
+        P.gsmem[g] = std::max(P.gsmem[g], sm);
+        P.smem = std::max(P.smem, sm);
+        P.opmask |= 1 << items[i].op;
         P.out_px += (double)it.h * it.w;
-        it.tiles_x = (it.w + tw - 1) / tw;
-        const long long tiles = (long long)it.tiles_x * ((it.h + th - 1) / th);
-        prefix[i] = (int)total;
-        total += tiles;
-        if (total > 0x7FFFFFFF) return KR_ERR_INVALID_ARG;
+    }
+    long long total = 0;
+    for (int g = 0; g < kGroups; ++g) {
+        P.first_tile[g] = (int)total;
+        for (int j = P.first_item[g]; j < P.first_item[g] + P.items[g]; ++j) {
+            prefix[j] = (int)total;
+            total += (long long)out[j].tiles_x * ((out[j].h + th - 1) / th);
+            if (total > 0x7FFFFFFF) return KR_ERR_INVALID_ARG;
+        }
+        P.tiles[g] = (int)total - P.first_tile[g];
     }
     prefix[n] = (int)total;
     P.total_tiles = (int)total;
@@ -294,21 +365,27 @@ struct Packed {
     PackInfo info;
 };
 
-static kr_status pack_items(const kr_work_t *items, int n, int tw, int th, Packed &P)
+static kr_status pack_items(const kr_work_t *items, int n, int tw, int th, int smem_cap, Packed &P)
 {
     P.items.resize(n);
     P.prefix.resize(n + 1);
-    return pack_into(items, n, tw, th, P.items.data(), P.prefix.data(), P.info);
+    return pack_into(items, n, tw, th, smem_cap, P.items.data(), P.prefix.data(), P.info);
 }
 
-// Work-list image: header, items, tile prefix (the layout the kernel reads).
-static void write_worklist_raw(const WorkItem *items, const int *prefix, int n, int total_tiles, uint8_t *dst)
+// Work-list image: header (with the group tables), items, tile prefix (the layout the
+// kernel reads).
+static void write_worklist_raw(const WorkItem *items, const int *prefix, int n, const PackInfo &P, uint8_t *dst)
 {
     WsHeader h;
     std::memset(&h, 0, sizeof(h));
-    h.next = 0;
     h.n = n;
-    h.total_tiles = total_tiles;
+    h.total_tiles = P.total_tiles;
+    for (int g = 0; g < kGroups; ++g) {
+        h.first_item[g] = P.first_item[g];
+        h.items[g] = P.items[g];
+        h.first_tile[g] = P.first_tile[g];
+        h.tiles[g] = P.tiles[g];
+    }
     std::memcpy(dst, &h, sizeof(h));
     std::memcpy(dst + sizeof(h), items, (size_t)n * sizeof(WorkItem));
     std::memcpy(dst + sizeof(h) + (size_t)n * sizeof(WorkItem), prefix, (size_t)(n + 1) * 4);
@@ -316,7 +393,7 @@ static void write_worklist_raw(const WorkItem *items, const int *prefix, int n, 
 
 static void write_worklist(const Packed &P, uint8_t *dst)
 {
-    write_worklist_raw(P.items.data(), P.prefix.data(), (int)P.items.size(), P.info.total_tiles, dst);
+    write_worklist_raw(P.items.data(), P.prefix.data(), (int)P.items.size(), P.info, dst);
 }
 
 // ---------------------------------------------------------------------------
@@ -330,12 +407,17 @@ struct GraphEntry {
     cudaGraphNode_t copy = nullptr;
 };
 
+// Side streams on which the kernels of further kinds run next to the first one.
+constexpr int kSide = 3;
+
 struct Ctx {
     size_t cap = 0;
     uint8_t *slot[kSlots] = {};
     cudaEvent_t done[kSlots] = {};
     int next = 0;
-    std::map<std::string, GraphEntry> graphs;   // key: stream|cfg|ctas
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork = nullptr, join[kSide] = {};
+    std::map<std::string, GraphEntry> graphs;   // key: stream|cfg|launch shapes
 };
 
 static std::mutex g_mu;
@@ -355,6 +437,14 @@ static void free_ctx(Ctx &c)
         c.done[i] = nullptr;
         c.slot[i] = nullptr;
     }
+    for (int i = 0; i < kSide; ++i) {
+        if (c.side[i]) { cudaStreamSynchronize(c.side[i]); cudaStreamDestroy(c.side[i]); }
+        if (c.join[i]) cudaEventDestroy(c.join[i]);
+        c.side[i] = nullptr;
+        c.join[i] = nullptr;
+    }
+    if (c.fork) cudaEventDestroy(c.fork);
+    c.fork = nullptr;
     c.cap = 0;
 }
 
@@ -369,6 +459,12 @@ static cudaError_t ctx_for(void *ws, size_t cap, Ctx *&out)
             e = cudaEventCreateWithFlags(&c.done[i], cudaEventDisableTiming);
             if (e != cudaSuccess) { free_ctx(c); return e; }
         }
+        cudaError_t e = cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming);
+        for (int i = 0; i < kSide && e == cudaSuccess; ++i) {
+            e = cudaStreamCreateWithFlags(&c.side[i], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.join[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) { free_ctx(c); return e; }
         c.cap = cap;
     }
     out = &c;
@@ -383,16 +479,90 @@ static int sm_count()
     return sms;
 }
 
-static cudaError_t prepare_cfg(int cfg, size_t smem, int &occ)
+// Shared-memory opt-in and residency of the kind-g kernel of configuration cfg.
+static cudaError_t prepare_kernel(int cfg, int g, size_t smem, int &occ)
 {
     const TileCfg &c = g_cfgs[cfg];
-    cudaError_t e = cudaFuncSetAttribute(c.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, c.max_smem);
+    cudaError_t e = cudaFuncSetAttribute(c.kernels[g], cudaFuncAttributeMaxDynamicSharedMemorySize, c.max_smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.kernel, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.kernels[g], kThreads, smem);
     if (e != cudaSuccess) return e;
     occ = std::max(occ, 1);
     return cudaSuccess;
 }
+
+// Launch shape of every kind present: grid (persistent, at most #SM x CTAs per SM) and
+// dynamic shared bytes. grid[g] = 0 for absent kinds.
+struct Launches {
+    int grid[kGroups] = {};
+    size_t smem[kGroups] = {};
+    int count = 0;
+    int min_occ = 1 << 30;   // fewest CTAs per SM among the kinds' kernels
+};
+
+static cudaError_t launch_shapes(const PackInfo &I, int cfg, int ctas_per_sm, Launches &L)
+{
+    L = Launches();
+    const int sms = sm_count();
+    for (int g = 0; g < kGroups; ++g) {
+        if (I.tiles[g] == 0) continue;
+        int occ = 1;
+        cudaError_t e = prepare_kernel(cfg, g, I.gsmem[g], occ);
+        if (e != cudaSuccess) return e;
+        L.min_occ = std::min(L.min_occ, occ);
+        const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
+        L.grid[g] = std::max(1, std::min(sms * per_sm, I.tiles[g]));
+        L.smem[g] = I.gsmem[g];
+        ++L.count;
+    }
+    return cudaSuccess;
+}
+
+// The kernels of a packed batch on `stream`, the work list already copied: the first kind
+// on the stream itself, the others on side streams forked after the copy and joined back,
+// so that the kinds run side by side. side == nullptr: all on the stream, one after another.
+static cudaError_t launch_kinds(const Launches &L, int cfg, void *ws, cudaStream_t stream, Ctx *side)
+{
+    cudaError_t e = cudaSuccess;
+    void *args[] = {&ws};
+    int k = 0;
+    if (side && L.count > 1) e = cudaEventRecord(side->fork, stream);
+    for (int g = 0; g < kGroups && e == cudaSuccess; ++g) {
+        if (!L.grid[g]) continue;
+        cudaStream_t s = stream;
+        if (side && k > 0) {
+            s = side->side[(k - 1) % kSide];
+            e = cudaStreamWaitEvent(s, side->fork, 0);
+        }
+        if (e == cudaSuccess)
+            e = cudaLaunchKernel(g_cfgs[cfg].kernels[g], dim3(L.grid[g]), dim3(kThreads), args, L.smem[g], s);
+        ++k;
+    }
+    if (side && L.count > 1)
+        for (int i = 0; i < std::min(kSide, L.count - 1) && e == cudaSuccess; ++i) {
+            e = cudaEventRecord(side->join[i], side->side[i]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, side->join[i], 0);
+        }
+    return e;
+}
+
+// Dynamic shared memory per CTA that lets k CTAs of configuration cfg share one SM.
+static int smem_cap_for(int cfg, int k)
+{
+    int dev = 0, per_sm = 0, reserved = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    cudaFuncAttributes fa;
+    std::memset(&fa, 0, sizeof(fa));
+    cudaFuncGetAttributes(&fa, g_cfgs[cfg].kernels[0]);   // every kind has the same static shared memory
+    long long cap = (long long)per_sm / std::max(k, 1) - reserved - (long long)fa.sharedSizeBytes;
+    cap = std::min<long long>(cap, g_cfgs[cfg].max_smem);
+    return cap > 0 ? (int)(cap & ~127LL) : 0;
+}
+
+// Residency the submit path targets when neither the caller nor the tuner chose one.
+constexpr int kDefaultCtasPerSm = 4;
 
 static std::string class_key(const Packed &P, int n)
 {
@@ -412,11 +582,9 @@ static kr_status enqueue(const Packed &P, void *ws, int cfg, int ctas_per_sm, bo
                          cudaStream_t stream, const char *where)
 {
     const size_t bytes = worklist_bytes((int)P.items.size());
-    int occ = 1;
-    cudaError_t e = prepare_cfg(cfg, P.info.smem, occ);
+    Launches L;
+    cudaError_t e = launch_shapes(P.info, cfg, ctas_per_sm, L);
     if (e != cudaSuccess) { set_last_error(where, e); return KR_ERR_CUDA; }
-    const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, occ) : occ;
-    const int grid = std::max(1, std::min(sm_count() * per_sm, P.info.total_tiles));
 
     std::lock_guard<std::mutex> lk(g_mu);
     Ctx *c = nullptr;
@@ -430,29 +598,36 @@ static kr_status enqueue(const Packed &P, void *ws, int cfg, int ctas_per_sm, bo
 
     if (!use_graph) {
         e = cudaMemcpyAsync(ws, c->slot[s], bytes, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess) {
-            void *args[] = {&ws};
-            e = cudaLaunchKernel(g_cfgs[cfg].kernel, dim3(grid), dim3(kThreads), args, P.info.smem, stream);
-        }
+        if (e == cudaSuccess) e = launch_kinds(L, cfg, ws, stream, c);
     } else {
-        char key[96];
-        std::snprintf(key, sizeof(key), "%p|%d|%d|%zu", (void *)stream, cfg, grid, P.info.smem);
+        // graph: the copy, then one kernel node per kind, all depending on the copy only
+        std::string key;
+        {
+            char b[64];
+            std::snprintf(b, sizeof(b), "%p|%d", (void *)stream, cfg);
+            key = b;
+            for (int g = 0; g < kGroups; ++g) {
+                std::snprintf(b, sizeof(b), "|%d:%zu", L.grid[g], L.smem[g]);
+                key += b;
+            }
+        }
         GraphEntry &g = c->graphs[key];
         if (!g.exec) {
             e = cudaGraphCreate(&g.graph, 0);
-            cudaGraphNode_t kn = nullptr;
             if (e == cudaSuccess)
                 e = cudaGraphAddMemcpyNode1D(&g.copy, g.graph, nullptr, 0, ws, c->slot[s], bytes,
                                              cudaMemcpyHostToDevice);
-            if (e == cudaSuccess) {
+            void *args[] = {&ws};
+            for (int k = 0; k < kGroups && e == cudaSuccess; ++k) {
+                if (!L.grid[k]) continue;
                 cudaKernelNodeParams kp;
                 std::memset(&kp, 0, sizeof(kp));
-                void *args[] = {&ws};
-                kp.func = (void *)g_cfgs[cfg].kernel;
-                kp.gridDim = dim3(grid);
+                kp.func = (void *)g_cfgs[cfg].kernels[k];
+                kp.gridDim = dim3(L.grid[k]);
                 kp.blockDim = dim3(kThreads);
-                kp.sharedMemBytes = (unsigned)P.info.smem;
+                kp.sharedMemBytes = (unsigned)L.smem[k];
                 kp.kernelParams = args;
+                cudaGraphNode_t kn = nullptr;
                 e = cudaGraphAddKernelNode(&kn, g.graph, &g.copy, 1, &kp);
             }
             if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, g.graph, 0);
@@ -545,19 +720,23 @@ kr_status kr_batch_submit(const kr_work_t *items, int32_t n, void *workspace, si
     kr_status st;
     if (cfg < 0) {
         // the cached choice for this batch class, else configuration 0
-        if ((st = pack_items(items, n, g_cfgs[0].tw, g_cfgs[0].th, P)) != KR_OK) return st;
+        const int k0 = ctas ? ctas : kDefaultCtasPerSm;
+        if ((st = pack_items(items, n, g_cfgs[0].tw, g_cfgs[0].th, smem_cap_for(0, k0), P)) != KR_OK) return st;
         const std::string key = class_key(P, n);
-        int c = 0, k = ctas;
+        int c = 0, k = k0;
         {
             std::lock_guard<std::mutex> lk(g_mu);
             auto it = g_tune.find(key);
             if (it != g_tune.end()) { c = it->second.first; if (!ctas) k = it->second.second; }
         }
+        if (c != 0 || k != k0)
+            if ((st = pack_items(items, n, g_cfgs[c].tw, g_cfgs[c].th, smem_cap_for(c, k), P)) != KR_OK) return st;
         cfg = c;
         ctas = k;
-        if (cfg != 0 && (st = pack_items(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th, P)) != KR_OK) return st;
-    } else if ((st = pack_items(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th, P)) != KR_OK) {
-        return st;
+    } else {
+        if (!ctas) ctas = kDefaultCtasPerSm;
+        if ((st = pack_items(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th, smem_cap_for(cfg, ctas), P)) != KR_OK)
+            return st;
     }
     // every item must fit in shared memory at this tile shape
     if (P.info.smem > (size_t)g_cfgs[cfg].max_smem) return KR_ERR_UNSUPPORTED;
@@ -578,28 +757,26 @@ kr_status kr_batch_submit_noalloc(const kr_work_t *items, int32_t n, const kr_ba
 
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     PackInfo P;
-    kr_status st = pack_into(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th, g_noalloc_items, g_noalloc_prefix, P);
+    kr_status st = pack_into(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th,
+                             smem_cap_for(cfg, ctas ? ctas : kDefaultCtasPerSm), g_noalloc_items,
+                             g_noalloc_prefix, P);
     if (st != KR_OK) return st;
     if (P.smem > (size_t)g_cfgs[cfg].max_smem) return KR_ERR_UNSUPPORTED;
-    int occ = 1;
+    Launches L;
     void *ws = nullptr;
-    cudaError_t e = prepare_cfg(cfg, P.smem, occ);
+    cudaError_t e = launch_shapes(P, cfg, ctas, L);
     if (e == cudaSuccess) e = noalloc_scratch_ptr(&ws);
     if (e != cudaSuccess) {
         set_last_error("kr_batch_submit_noalloc", e);
         return KR_ERR_CUDA;
     }
-    const int per_sm = ctas > 0 ? std::min(ctas, occ) : occ;
-    const int grid = std::max(1, std::min(sm_count() * per_sm, P.total_tiles));
     const size_t bytes = worklist_bytes(n);
-    write_worklist_raw(g_noalloc_items, g_noalloc_prefix, n, P.total_tiles, g_noalloc_host);
+    write_worklist_raw(g_noalloc_items, g_noalloc_prefix, n, P, g_noalloc_host);
     // Pageable source: the call returns once the bytes are out of g_noalloc_host, so the
-    // next call may overwrite it. The copy also clears the header's tile counter.
+    // next call may overwrite it. The copy also clears the header's tile counters. The
+    // kinds' kernels run one after another on the stream (no side streams here).
     e = cudaMemcpyAsync(ws, g_noalloc_host, bytes, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) {
-        void *args[] = {&ws};
-        e = cudaLaunchKernel(g_cfgs[cfg].kernel, dim3(grid), dim3(kThreads), args, P.smem, s);
-    }
+    if (e == cudaSuccess) e = launch_kinds(L, cfg, ws, s, nullptr);
     if (e != cudaSuccess) {
         set_last_error("kr_batch_submit_noalloc", e);
         return KR_ERR_CUDA;
@@ -619,16 +796,18 @@ kr_status kr_autotune_batch(const kr_work_t *items, int32_t n, void *workspace, 
     int bc = 0, bk = 0;
     std::string key;
     kr_status result = KR_OK;
+    static const int kCands[] = {1, 2, 3, 4, 6, 8};
     for (int cfg = 0; cfg < kNumCfgs && result == KR_OK; ++cfg) {
-        Packed P;
-        kr_status st = pack_items(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th, P);
-        if (st != KR_OK) { result = st; break; }
-        if (cfg == 0) key = class_key(P, n);
-        if (P.info.smem > (size_t)g_cfgs[cfg].max_smem) continue;
-        int occ = 1;
-        if (prepare_cfg(cfg, P.info.smem, occ) != cudaSuccess) { result = KR_ERR_CUDA; break; }
-        for (int k = 1; k <= occ; ++k) {
-            if (k > 2 && k < occ) continue;   // candidates: 1, 2 and the occupancy limit
+        for (int k : kCands) {
+            // each residency target packs the batch with its own shared-memory cap
+            Packed P;
+            kr_status st = pack_items(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th, smem_cap_for(cfg, k), P);
+            if (st == KR_ERR_NO_SPACE) continue;   // an output stage alone exceeds the cap
+            if (st != KR_OK) { result = st; break; }
+            if (key.empty()) key = class_key(P, n);   // the class does not depend on cfg or k
+            Launches L;
+            if (launch_shapes(P.info, cfg, k, L) != cudaSuccess) { result = KR_ERR_CUDA; break; }
+            if (L.min_occ < k) continue;   // registers (or the cap's rounding) allow fewer CTAs
             float ms_best = 1e30f;
             for (int rep = 0; rep < 4 && result == KR_OK; ++rep) {
                 cudaEventRecord(e0, s);
