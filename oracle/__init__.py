@@ -61,6 +61,8 @@ def _load():
             lib.oracle_rgb_to_gray_u8.argtypes = [_u8p, _L, _L, _u8p]
             lib.oracle_warp_point.argtypes = [_f32p, _L, _L, _f32p, _f32p, _lp, _lp, _lp, _lp]
             lib.oracle_resize_point.argtypes = [_L, _L, _L, _lp, _lp, _lp, _f64p]
+            lib.oracle_resize_nearest_u8.argtypes = [_u8p, _L, _L, _L, _u8p, _L, _L]
+            lib.oracle_flip_h_u8.argtypes = [_u8p, _L, _L, _L, _u8p]
             for f in (lib.oracle_resize_u8, lib.oracle_resize_f64, lib.oracle_warp_u8,
                       lib.oracle_warp_f64, lib.oracle_rgb_to_gray_u8, lib.oracle_warp_point,
                       lib.oracle_resize_point):
@@ -164,6 +166,28 @@ def rgb_to_gray_u8(img):
     rc = _load().oracle_rgb_to_gray_u8(_p(src, _u8p), H, W, _p(out, _u8p))
     if rc != 0:
         raise ValueError("oracle_rgb_to_gray_u8: bad arguments")
+    return out
+
+
+def resize_nearest_u8(img, h, w):
+    """Nearest-neighbour resize (half-pixel centres) of an H x W x C u8 image to h x w."""
+    src = _src(img)
+    H, W, C = src.shape
+    out = np.zeros((h, w, C), dtype=np.uint8)
+    rc = _load().oracle_resize_nearest_u8(_p(src, _u8p), H, W, C, _p(out, _u8p), h, w)
+    if rc != 0:
+        raise ValueError("oracle_resize_nearest_u8: bad arguments")
+    return out
+
+
+def flip_h_u8(img):
+    """Horizontal flip of an H x W x C u8 image."""
+    src = _src(img)
+    H, W, C = src.shape
+    out = np.zeros((H, W, C), dtype=np.uint8)
+    rc = _load().oracle_flip_h_u8(_p(src, _u8p), H, W, C, _p(out, _u8p))
+    if rc != 0:
+        raise ValueError("oracle_flip_h_u8: bad arguments")
     return out
 
 

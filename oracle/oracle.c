@@ -13,7 +13,9 @@
  *     of kornia-imgproc), u8 fixed-point and f64 forms;
  *   - RGB -> gray (Sec. III "RGB to grayscale"; Sec. IV-B gray_from_rgb),
  *     standalone and fused after either resampler;
- *   - u8 -> float normalisation (value/255 - mean)/std, fused.
+ *   - u8 -> float normalisation (value/255 - mean)/std, fused;
+ *   - nearest-neighbour resize (Sec. IV-A, the Python bindings' "nearest-
+ *     neighbor resizing") and horizontal flip (Sec. IV-A, Rust benchmark).
  *
  * The paper prints none of the arithmetic. The conventions used here are:
  *   half-pixel centres; resize clamps to the edge; warp reads zero outside the
@@ -346,5 +348,41 @@ int oracle_resize_point(long i, long n_in, long n_out, long *i0, long *i1,
 {
     if (n_in < 1 || n_out < 1 || i < 0 || i >= n_out) return ORACLE_BAD;
     resize_axis(i, n_in, n_out, i0, i1, q, frac);
+    return ORACLE_OK;
+}
+
+/* ======================================================================== */
+/* Nearest-neighbour resize, u8, C = 1 or 3 (Sec. IV-A names the operation, */
+/* not its convention). With half-pixel centres the output pixel (x, y) has */
+/* its centre at source position ((x + 1/2) W / w, (y + 1/2) H / h) in      */
+/* continuous coordinates where source pixel i covers [i, i + 1); it copies */
+/* the source pixel covering that point:                                    */
+/*     sx = floor((x + 1/2) W / w) = ((2x + 1) W) div (2w),  likewise sy,   */
+/* exact integer arithmetic, never outside [0, W - 1] x [0, H - 1].         */
+/* ======================================================================== */
+int oracle_resize_nearest_u8(const uint8_t *src, long H, long W, long C, uint8_t *dst, long h, long w)
+{
+    if (H < 1 || W < 1 || h < 1 || w < 1 || (C != 1 && C != 3)) return ORACLE_BAD;
+    for (long y = 0; y < h; ++y) {
+        const long sy = (long)(((2LL * y + 1LL) * (long long)H) / (2LL * (long long)h));
+        for (long x = 0; x < w; ++x) {
+            const long sx = (long)(((2LL * x + 1LL) * (long long)W) / (2LL * (long long)w));
+            for (long c = 0; c < C; ++c)
+                dst[(y * w + x) * C + c] = src[(sy * W + sx) * C + c];
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* ======================================================================== */
+/* Horizontal flip, u8, C = 1 or 3 (Sec. IV-A): out(y, x) = in(y, W - 1 - x) */
+/* ======================================================================== */
+int oracle_flip_h_u8(const uint8_t *src, long H, long W, long C, uint8_t *dst)
+{
+    if (H < 1 || W < 1 || (C != 1 && C != 3)) return ORACLE_BAD;
+    for (long y = 0; y < H; ++y)
+        for (long x = 0; x < W; ++x)
+            for (long c = 0; c < C; ++c)
+                dst[(y * W + x) * C + c] = src[(y * W + (W - 1 - x)) * C + c];
     return ORACLE_OK;
 }

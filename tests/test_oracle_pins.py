@@ -351,3 +351,54 @@ def test_touched_sparse_downscale_counts_rows_and_columns():
     # sector-granular count is at least the pixel count and at most 2 sectors per pixel
     sec = oracle.touched_bytes(t, 3, sector=32)
     assert len(rows) * len(cols) * 3 <= sec <= len(rows) * len(cols) * 2 * 32
+
+
+# ---------------------------------------------------------------------------
+# Nearest-neighbour resize and horizontal flip
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("C", [1, 3])
+def test_nearest_same_size_is_identity(C):
+    img = inputs.uniform_image(70, 23, 41, C)
+    np.testing.assert_array_equal(oracle.resize_nearest_u8(img, 23, 41), img)
+
+
+@pytest.mark.parametrize("ky,kx", [(2, 2), (3, 1), (1, 4), (5, 3)])
+def test_nearest_integer_upscale_repeats_each_pixel(ky, kx):
+    img = inputs.uniform_image(71, 9, 13, 3)
+    ref = np.repeat(np.repeat(img, ky, axis=0), kx, axis=1)
+    np.testing.assert_array_equal(oracle.resize_nearest_u8(img, 9 * ky, 13 * kx), ref)
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 7])
+def test_nearest_integer_downscale_takes_the_centre_pixel_of_each_block(k):
+    # each k x k block's centre lies in pixel k // 2 of the block
+    img = inputs.uniform_image(72, 5 * k, 6 * k, 3)
+    ref = img[k // 2::k, k // 2::k]
+    np.testing.assert_array_equal(oracle.resize_nearest_u8(img, 5, 6), ref)
+
+
+def test_nearest_brute_force_exact_rationals():
+    rng = np.random.default_rng(73)
+    for _ in range(12):
+        H, W, h, w = (int(v) for v in rng.integers(1, 40, 4))
+        img = inputs.uniform_image(int(rng.integers(1 << 30)), H, W, 3)
+        got = oracle.resize_nearest_u8(img, h, w)
+        ys = [math.floor((Fraction(y) + Fraction(1, 2)) * H / h) for y in range(h)]
+        xs = [math.floor((Fraction(x) + Fraction(1, 2)) * W / w) for x in range(w)]
+        np.testing.assert_array_equal(got, img[np.ix_(ys, xs)])
+
+
+@pytest.mark.parametrize("C", [1, 3])
+def test_flip_reverses_columns_and_is_an_involution(C):
+    img = inputs.uniform_image(74, 17, 29, C)
+    f = oracle.flip_h_u8(img)
+    np.testing.assert_array_equal(f, img[:, ::-1])
+    np.testing.assert_array_equal(oracle.flip_h_u8(f), img)
+
+
+def test_flip_equals_the_warp_with_the_mirror_map():
+    # the inverse map x_src = W - 1 - x has zero fraction: the bilinear warp copies pixels
+    H, W = 19, 31
+    img = inputs.uniform_image(75, H, W, 3)
+    M = np.array([[-1, 0, W], [0, 1, 0]], np.float32)
+    np.testing.assert_array_equal(oracle.flip_h_u8(img), oracle.warp_u8(img, M, H, W))
