@@ -305,6 +305,41 @@ def serving_compare(torch, kr, dev, rates=(2000, 5000, 10000, 20000, 40000, 8000
     return out
 
 
+def next_rows(torch, kr, dev, imgs_dev, peak, reps=50):
+    """The widening rows on the same frames, each one launch over the batch: nearest-neighbour
+    resize -> 1280x720 and horizontal flip. Algorithmic bytes = output + distinct source pixels
+    read (nearest: distinct source rows x distinct source columns; flip: every pixel)."""
+    n, H, W, C = imgs_dev.shape
+    lib = kr.load()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    s = kr.image(imgs_dev)
+    outs = {"resize_nearest_u8": torch.empty((n, RS_H, RS_W, C), dtype=torch.uint8, device=dev),
+            "flip_u8": torch.empty((n, H, W, C), dtype=torch.uint8, device=dev)}
+    ds = {k: kr.image(v) for k, v in outs.items()}
+    calls = {"resize_nearest_u8": lambda: lib.kr_resize_nearest(ctypes.byref(s), ctypes.byref(ds["resize_nearest_u8"]), st),
+             "flip_u8": lambda: lib.kr_flip_horizontal(ctypes.byref(s), ctypes.byref(ds["flip_u8"]), st)}
+    rows = len({((2 * y + 1) * H) // (2 * RS_H) for y in range(RS_H)})
+    cols = len({((2 * x + 1) * W) // (2 * RS_W) for x in range(RS_W)})
+    alg = {"resize_nearest_u8": n * (RS_H * RS_W * C + rows * cols * C), "flip_u8": n * 2 * H * W * C}
+    res = {}
+    for name, fn in calls.items():
+        for _ in range(3):
+            assert fn() == 0
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / reps
+        gbs = alg[name] / (ms * 1e-3) / 1e9
+        res[name] = {"ms": round(ms, 4), "alg_bytes": alg[name], "GB_s": round(gbs, 1),
+                     "frac_of_measured_hbm": round(gbs / peak, 3),
+                     "gpx_s": round(n * outs[name].shape[1] * outs[name].shape[2] / (ms * 1e-3) / 1e9, 1)}
+    return res
+
+
 def cpu_baseline_sample(budget_s=12.0):
     """The oracle (single-threaded C) on a bounded sample of the step: whole frames, all eight
     operations, until the time budget is spent."""
@@ -434,6 +469,7 @@ def run_gpu(args):
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 3),
            "steps": K_e2e}
 
+    widening = next_rows(torch, kr, dev, imgs_dev, peak)
     ragged = ragged_compare(torch, kr, dev) if not args.no_extras else None
     serving = serving_compare(torch, kr, dev, seconds=args.serve_seconds) if not args.no_extras else None
     cpu = cpu_baseline_sample() if (rank == 0 and not args.no_extras) else None
@@ -449,7 +485,8 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "no flush: 199 MB of distinct source frames per step > 129 MB L2"},
             "roofline": roofline, "per_op": breakdown, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": K * len(ops), "ragged": ragged, "serving": serving, "clocks": clk.summary(),
+            "gpu_launches": K * len(ops), "next_rows": widening, "ragged": ragged, "serving": serving,
+            "clocks": clk.summary(),
         }
         print(json.dumps(line))
     if world > 1:

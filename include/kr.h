@@ -139,6 +139,23 @@ kr_status kr_warp_affine(const kr_image_t *src, const kr_image_t *dst, const flo
  */
 kr_status kr_rgb_to_gray(const kr_image_t *src, const kr_image_t *dst, kr_stream_t stream);
 
+/*
+ * Nearest-neighbour resize (Sec. IV-A: the Python bindings' "nearest-neighbor
+ * resizing"; the paper gives no convention). Half-pixel centres: output pixel
+ * (x, y) copies source pixel (((2x + 1) W) div (2w), ((2y + 1) H) div (2h)),
+ * the one covering the output pixel's centre. src, dst: u8 HWC, the same
+ * channels (1 or 3) and batch; dst's size is the output size. Bit-exact copy of
+ * source bytes. Errors as for kr_resize_bilinear; nothing is enqueued on error.
+ */
+kr_status kr_resize_nearest(const kr_image_t *src, const kr_image_t *dst, kr_stream_t stream);
+
+/*
+ * Horizontal flip (Sec. IV-A, one of the geometric transforms of the Rust
+ * benchmark): dst(y, x) = src(y, W - 1 - x). src, dst: u8 HWC, the same size,
+ * channels (1 or 3) and batch, not overlapping (KR_ERR_ALIAS: no in-place flip).
+ */
+kr_status kr_flip_horizontal(const kr_image_t *src, const kr_image_t *dst, kr_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Ragged batch: many independent operations in one persistent launch.      */
 /* ------------------------------------------------------------------------ */

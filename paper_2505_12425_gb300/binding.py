@@ -95,6 +95,8 @@ def load():
         lib.kr_resize_bilinear.argtypes = [P(KrImage), P(KrImage), P(KrPost), ctypes.c_void_p]
         lib.kr_warp_affine.argtypes = [P(KrImage), P(KrImage), P(ctypes.c_float), P(KrPost), ctypes.c_void_p]
         lib.kr_rgb_to_gray.argtypes = [P(KrImage), P(KrImage), ctypes.c_void_p]
+        lib.kr_resize_nearest.argtypes = [P(KrImage), P(KrImage), ctypes.c_void_p]
+        lib.kr_flip_horizontal.argtypes = [P(KrImage), P(KrImage), ctypes.c_void_p]
         lib.kr_batch_workspace_size.argtypes = [ctypes.c_int32]
         lib.kr_batch_workspace_size.restype = ctypes.c_size_t
         lib.kr_batch_submit.argtypes = [P(KrWork), ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t,
@@ -115,7 +117,8 @@ def load():
         lib.kr_last_error.restype = ctypes.c_char_p
         lib.kr_shutdown.argtypes = []
         lib.kr_shutdown.restype = None
-        for f in ("kr_resize_bilinear", "kr_warp_affine", "kr_rgb_to_gray", "kr_batch_submit",
+        for f in ("kr_resize_bilinear", "kr_warp_affine", "kr_rgb_to_gray", "kr_resize_nearest",
+                  "kr_flip_horizontal", "kr_batch_submit",
                   "kr_batch_submit_noalloc", "kr_serve_run", "kr_device_errors",
                   "kr_tile_config_shape", "kr_autotune_batch", "kr_autotune_save", "kr_autotune_load"):
             getattr(lib, f).restype = S
@@ -223,6 +226,20 @@ def kr_rgb_to_gray(src, dst, stream=None):
     lib = load()
     s, d = image(src), image(dst)
     _check(lib.kr_rgb_to_gray(ctypes.byref(s), ctypes.byref(d), _stream(stream)), "kr_rgb_to_gray")
+
+
+def kr_resize_nearest(src, dst, stream=None):
+    """Nearest-neighbour resize (half-pixel centres) of u8 HWC `src` into u8 `dst`."""
+    lib = load()
+    s, d = image(src), image(dst)
+    _check(lib.kr_resize_nearest(ctypes.byref(s), ctypes.byref(d), _stream(stream)), "kr_resize_nearest")
+
+
+def kr_flip_horizontal(src, dst, stream=None):
+    """Horizontal flip of u8 HWC `src` into `dst` of the same size (not in place)."""
+    lib = load()
+    s, d = image(src), image(dst)
+    _check(lib.kr_flip_horizontal(ctypes.byref(s), ctypes.byref(d), _stream(stream)), "kr_flip_horizontal")
 
 
 def work_item(op, src, dst, M=None, gray=False, mean=None, std=None, dst_layout="hwc") -> KrWork:

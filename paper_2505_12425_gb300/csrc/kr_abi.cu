@@ -153,11 +153,64 @@ kr_status build_gray(const kr_image_t *src, const kr_image_t *dst, GrayDesc &d)
     return KR_OK;
 }
 
+// Validate a pixel gather (u8 HWC in and out, same channels and batch; the flip keeps
+// the size) and fill its descriptor.
+static kr_status build_gather(const kr_image_t *src, const kr_image_t *dst, bool same_size, GatherDesc &d)
+{
+    kr_status st;
+    if ((st = check_image(src, false)) != KR_OK) return st;
+    if ((st = check_image(dst, true)) != KR_OK) return st;
+    if (src->dtype != KR_U8 || dst->dtype != KR_U8 || src->layout != KR_HWC || dst->layout != KR_HWC)
+        return KR_ERR_UNSUPPORTED;
+    if (src->channels != dst->channels || src->batch != dst->batch) return KR_ERR_INVALID_ARG;
+    if (same_size && (src->height != dst->height || src->width != dst->width)) return KR_ERR_INVALID_ARG;
+    if ((st = check_alias(*src, *dst)) != KR_OK) return st;
+    d.src = (const uint8_t *)src->data;
+    d.spitch = src->pitch;
+    d.sbatch = src->batch > 1 ? src->batch_stride : 0;
+    d.H = src->height;
+    d.W = src->width;
+    d.dst = (uint8_t *)dst->data;
+    d.dpitch = dst->pitch;
+    d.dbatch = dst->batch > 1 ? dst->batch_stride : 0;
+    d.h = dst->height;
+    d.w = dst->width;
+    d.C = src->channels;
+    d.batch = src->batch;
+    return KR_OK;
+}
+
 }  // namespace kr
 
 using namespace kr;
 
 extern "C" {
+
+kr_status kr_resize_nearest(const kr_image_t *src, const kr_image_t *dst, kr_stream_t stream)
+{
+    GatherDesc d;
+    kr_status st = build_gather(src, dst, false, d);
+    if (st != KR_OK) return st;
+    cudaError_t e = launch_resize_nearest(d, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_last_error("kr_resize_nearest", e);
+        return KR_ERR_CUDA;
+    }
+    return KR_OK;
+}
+
+kr_status kr_flip_horizontal(const kr_image_t *src, const kr_image_t *dst, kr_stream_t stream)
+{
+    GatherDesc d;
+    kr_status st = build_gather(src, dst, true, d);
+    if (st != KR_OK) return st;
+    cudaError_t e = launch_flip_h(d, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_last_error("kr_flip_horizontal", e);
+        return KR_ERR_CUDA;
+    }
+    return KR_OK;
+}
 
 kr_status kr_resize_bilinear(const kr_image_t *src, const kr_image_t *dst, const kr_post_t *post,
                              kr_stream_t stream)

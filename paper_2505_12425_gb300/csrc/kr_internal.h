@@ -48,6 +48,20 @@ struct GrayDesc {
 };
 cudaError_t launch_gray(const GrayDesc &d, cudaStream_t stream);
 
+// Pixel gathers (nearest-neighbour resize, horizontal flip): u8 HWC, C = 1 or 3.
+struct GatherDesc {
+    const uint8_t *src;
+    int64_t spitch, sbatch;
+    int H, W;
+    uint8_t *dst;
+    int64_t dpitch, dbatch;
+    int h, w;
+    int C;
+    int batch;
+};
+cudaError_t launch_resize_nearest(const GatherDesc &d, cudaStream_t stream);
+cudaError_t launch_flip_h(const GatherDesc &d, cudaStream_t stream);
+
 // Shared-memory budget of one tile: region A bytes (0 = no staging) and region B bytes
 // (at least out_bytes, the output tile). Multiples of 16.
 inline int round128(int x) { return (x + 127) & ~127; }

@@ -98,6 +98,17 @@ def test_warp_rejects_nonfinite_matrix(lib):
     assert lib.kr_warp_affine(ctypes.byref(s), ctypes.byref(d), None, ctypes.byref(p), None) == 1
 
 
+def test_gathers_reject_bad_shapes(lib):
+    s = _img()
+    for f in (lib.kr_resize_nearest, lib.kr_flip_horizontal):
+        assert f(ctypes.byref(s), ctypes.byref(_img(data=0x900000, c=1)), None) == 1       # channels differ
+        assert f(ctypes.byref(s), ctypes.byref(_img(data=0x10001, c=3)), None) == 3        # overlap
+        assert f(None, ctypes.byref(_img(data=0x900000, c=3)), None) == 1
+    assert lib.kr_flip_horizontal(ctypes.byref(s), ctypes.byref(_img(data=0x900000, c=3, w=4)), None) == 1
+    f32 = _img(data=0x900000, c=3, dtype=kr.KR_F32)
+    assert lib.kr_resize_nearest(ctypes.byref(s), ctypes.byref(f32), None) == 2
+
+
 def test_gray_rejects_bad_shapes(lib):
     s = _img()
     assert lib.kr_rgb_to_gray(ctypes.byref(s), ctypes.byref(_img(data=0x900000, c=3)), None) == 1

@@ -342,3 +342,69 @@ def test_errors_do_not_enqueue():
     assert e.value.status == 3
     with pytest.raises(kr.KrError):
         kr.kr_warp_affine(src, src.clone(), [np.nan, 0, 0, 0, 1, 0])
+
+
+# ---------------------------------------------------------------------------
+# Nearest-neighbour resize and horizontal flip (pixel gathers)
+# ---------------------------------------------------------------------------
+NEAREST_CASES = [
+    (480, 640, 240, 320, 3), (1080, 1920, 720, 1280, 3), (37, 53, 91, 17, 3), (100, 100, 33, 47, 1),
+    (1, 1, 5, 7, 3), (1, 300, 1, 257, 3), (300, 1, 257, 1, 1), (64, 64, 64, 64, 3), (2160, 3840, 224, 224, 3),
+    (33, 65, 130, 258, 1), (257, 129, 65, 97, 3),
+]
+
+
+@pytest.mark.parametrize("H,W,h,w,C", NEAREST_CASES)
+def test_resize_nearest(H, W, h, w, C):
+    img = inputs.uniform_image(H * 7 + W, H, W, C)
+    out = Guarded((h, w, C), torch.uint8)
+    kr.kr_resize_nearest(to_dev(img), out.t)
+    torch.cuda.synchronize()
+    out.check()
+    np.testing.assert_array_equal(out.np(), oracle.resize_nearest_u8(img, h, w))
+
+
+@pytest.mark.parametrize("H,W,C", [(1080, 1920, 3), (17, 29, 3), (1, 1, 3), (5, 301, 1), (300, 2, 3)])
+def test_flip_horizontal(H, W, C):
+    img = inputs.uniform_image(H + 3 * W, H, W, C)
+    out = Guarded((H, W, C), torch.uint8)
+    kr.kr_flip_horizontal(to_dev(img), out.t)
+    torch.cuda.synchronize()
+    out.check()
+    np.testing.assert_array_equal(out.np(), oracle.flip_h_u8(img))
+    back = torch.empty_like(out.t)
+    kr.kr_flip_horizontal(out.t, back)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(back.cpu().numpy(), img)
+
+
+def test_gathers_on_views_and_batches():
+    n, H, W = 3, 41, 77
+    imgs = np.stack([inputs.uniform_image(80 + i, H, W, 3) for i in range(n)])
+    big = torch.full((n, H + 4, W + 5, 3), 9, dtype=torch.uint8, device=dev())
+    big[:, 2:2 + H, 3:3 + W] = to_dev(imgs)
+    src = big[:, 2:2 + H, 3:3 + W]                                   # odd pitch and offset
+    dbig = torch.full((n, 60, 90, 3), CANARY_U8, dtype=torch.uint8, device=dev())
+    nd = dbig[:, 1:1 + 50, 2:2 + 63]
+    fd = torch.full((n, H, W, 3), CANARY_U8, dtype=torch.uint8, device=dev())
+    kr.kr_resize_nearest(src, nd)
+    kr.kr_flip_horizontal(src, fd)
+    torch.cuda.synchronize()
+    m = torch.ones(dbig.shape[:3], dtype=torch.bool, device=dev())
+    m[:, 1:51, 2:65] = False
+    assert bool((dbig[m] == CANARY_U8).all()), "write outside the destination view"
+    for i in range(n):
+        np.testing.assert_array_equal(nd[i].cpu().numpy(), oracle.resize_nearest_u8(imgs[i], 50, 63))
+        np.testing.assert_array_equal(fd[i].cpu().numpy(), oracle.flip_h_u8(imgs[i]))
+
+
+def test_flip_equals_warp_with_the_mirror_map():
+    H, W = 90, 131
+    img = inputs.noise_gradient_image(81, H, W)
+    M = np.array([[-1, 0, W], [0, 1, 0]], np.float32)
+    f = torch.empty((H, W, 3), dtype=torch.uint8, device=dev())
+    w = torch.empty_like(f)
+    kr.kr_flip_horizontal(to_dev(img), f)
+    kr.kr_warp_affine(to_dev(img), w, M)
+    torch.cuda.synchronize()
+    assert torch.equal(f, w)
