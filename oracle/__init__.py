@@ -62,6 +62,10 @@ def _load():
             lib.oracle_warp_point.argtypes = [_f32p, _L, _L, _f32p, _f32p, _lp, _lp, _lp, _lp]
             lib.oracle_resize_point.argtypes = [_L, _L, _L, _lp, _lp, _lp, _f64p]
             lib.oracle_resize_nearest_u8.argtypes = [_u8p, _L, _L, _L, _u8p, _L, _L]
+            lib.oracle_warp_persp_u8.argtypes = [_u8p, _L, _L, _L, _f32p, _u8p, _L, _L, ctypes.c_int, _u8p]
+            lib.oracle_warp_persp_f64.argtypes = [_u8p, _L, _L, _L, _f32p, _f64p, _L, _L, ctypes.c_int,
+                                                  _f64p, _f64p, _u8p]
+            lib.oracle_persp_point.argtypes = [_f32p, _L, _L, _f32p, _f32p, _lp, _lp, _lp, _lp]
             lib.oracle_flip_h_u8.argtypes = [_u8p, _L, _L, _L, _u8p]
             for f in (lib.oracle_resize_u8, lib.oracle_resize_f64, lib.oracle_warp_u8,
                       lib.oracle_warp_f64, lib.oracle_rgb_to_gray_u8, lib.oracle_warp_point,
@@ -122,8 +126,8 @@ def resize_f64(img, h, w, gray=False, mean=None, std=None, touched=False):
     return (out, t) if touched else out
 
 
-def _mat(M):
-    M = np.ascontiguousarray(np.asarray(M, dtype=np.float32).reshape(6))
+def _mat(M, n=6):
+    M = np.ascontiguousarray(np.asarray(M, dtype=np.float32).reshape(n))
     return M
 
 
@@ -189,6 +193,46 @@ def flip_h_u8(img):
     if rc != 0:
         raise ValueError("oracle_flip_h_u8: bad arguments")
     return out
+
+
+def warp_persp_u8(img, M, h, w, gray=False, touched=False):
+    """Perspective warp (M: 3x3 destination->source, fp32), zero border, u8 fixed point."""
+    src = _src(img)
+    H, W, C = src.shape
+    Mf = _mat(M, 9)
+    out = np.zeros((h, w, 1 if gray else C), dtype=np.uint8)
+    t = _touched(H, W, touched)
+    rc = _load().oracle_warp_persp_u8(_p(src, _u8p), H, W, C, _p(Mf, _f32p), _p(out, _u8p), h, w,
+                                      int(gray), _p(t, _u8p))
+    if rc != 0:
+        raise ValueError("oracle_warp_persp_u8: bad arguments")
+    return (out, t) if touched else out
+
+
+def warp_persp_f64(img, M, h, w, gray=False, mean=None, std=None, touched=False):
+    """Perspective warp of p/255 in double (fp32 coordinate), zero border, normalised."""
+    src = _src(img)
+    H, W, C = src.shape
+    Mf = _mat(M, 9)
+    m, s = _norm(C, mean, std)
+    out = np.zeros((h, w, 1 if gray else C), dtype=np.float64)
+    t = _touched(H, W, touched)
+    rc = _load().oracle_warp_persp_f64(_p(src, _u8p), H, W, C, _p(Mf, _f32p), _p(out, _f64p), h, w,
+                                       int(gray), _p(m, _f64p), _p(s, _f64p), _p(t, _u8p))
+    if rc != 0:
+        raise ValueError("oracle_warp_persp_f64: bad arguments")
+    return (out, t) if touched else out
+
+
+def persp_point(M, x, y):
+    """(ok, sx, sy, x0, qx, y0, qy) of output pixel (x, y) under the 3x3 map M."""
+    Mf = _mat(M, 9)
+    sx, sy = ctypes.c_float(), ctypes.c_float()
+    x0, qx, y0, qy = ctypes.c_long(), ctypes.c_long(), ctypes.c_long(), ctypes.c_long()
+    ok = _load().oracle_persp_point(_p(Mf, _f32p), x, y, ctypes.byref(sx), ctypes.byref(sy),
+                                    ctypes.byref(x0), ctypes.byref(qx), ctypes.byref(y0),
+                                    ctypes.byref(qy))
+    return bool(ok), sx.value, sy.value, x0.value, qx.value, y0.value, qy.value
 
 
 def warp_point(M, x, y):

@@ -15,7 +15,10 @@
  *     standalone and fused after either resampler;
  *   - u8 -> float normalisation (value/255 - mean)/std, fused;
  *   - nearest-neighbour resize (Sec. IV-A, the Python bindings' "nearest-
- *     neighbor resizing") and horizontal flip (Sec. IV-A, Rust benchmark).
+ *     neighbor resizing") and horizontal flip (Sec. IV-A, Rust benchmark);
+ *   - perspective warp with a 3x3 inverse map (the projective generalisation
+ *     of the affine warp; Sec. II-A "geometric transforms"), same taps,
+ *     weights and border as the affine warp.
  *
  * The paper prints none of the arithmetic. The conventions used here are:
  *   half-pixel centres; resize clamps to the edge; warp reads zero outside the
@@ -201,6 +204,32 @@ static int warp_coord(const float *M, long x, long y, float *sx, float *sy)
     return (fabsf(*sx) < 4194304.0f) && (fabsf(*sy) < 4194304.0f);
 }
 
+/* Perspective coordinate: M (3x3, row-major) maps destination -> source in */
+/* homogeneous coordinates. fp32, round to nearest, exactly as written:      */
+/*   X, Y, Z = fmaf(m_r0, xc, fmaf(m_r1, yc, m_r2)) for rows r = 0, 1, 2;    */
+/*   q = 1 / Z; sx = X * q - 0.5; sy = Y * q - 0.5.                          */
+/* A point with Z <= 0 (or NaN) has no source: zero sample, as is a sample  */
+/* beyond |s| < 2^22. With the last row (0, 0, 1), q = 1 and X * q = X, so  */
+/* the affine warp is the special case bit for bit.                         */
+static int persp_coord(const float *M, long x, long y, float *sx, float *sy)
+{
+    float xc = (float)x + 0.5f;
+    float yc = (float)y + 0.5f;
+    float X = fmaf(M[0], xc, fmaf(M[1], yc, M[2]));
+    float Y = fmaf(M[3], xc, fmaf(M[4], yc, M[5]));
+    float Z = fmaf(M[6], xc, fmaf(M[7], yc, M[8]));
+    if (!(Z > 0.0f)) return 0;
+    float q = 1.0f / Z;
+    *sx = X * q - 0.5f;
+    *sy = Y * q - 0.5f;
+    return (fabsf(*sx) < 4194304.0f) && (fabsf(*sy) < 4194304.0f);
+}
+
+static int coord_of(const float *M, int persp, long x, long y, float *sx, float *sy)
+{
+    return persp ? persp_coord(M, x, y, sx, sy) : warp_coord(M, x, y, sx, sy);
+}
+
 /* 11-bit weight of a coordinate: floor and round-half-up of 2048 * frac,   */
 /* all in fp32 exactly as written.                                          */
 static void warp_weight(float s, long *i0, long *q)
@@ -225,10 +254,11 @@ static void mark_in(uint8_t *touched, long H, long W, long y, long x)
 }
 
 /* ======================================================================== */
-/* Affine warp, u8 out (zero border per tap). M: 6 floats, row-major 2x3.   */
+/* Affine (persp = 0; M: 6 floats, row-major 2x3) or perspective (persp = 1; */
+/* M: 9 floats, row-major 3x3) warp, u8 out (zero border per tap).          */
 /* ======================================================================== */
-int oracle_warp_u8(const uint8_t *src, long H, long W, long C, const float *M,
-                   uint8_t *dst, long h, long w, int gray, uint8_t *touched)
+static int warp_u8_impl(const uint8_t *src, long H, long W, long C, const float *M, int persp,
+                        uint8_t *dst, long h, long w, int gray, uint8_t *touched)
 {
     if (H < 1 || W < 1 || h < 1 || w < 1 || (C != 1 && C != 3)) return ORACLE_BAD;
     if (gray && C != 3) return ORACLE_BAD;
@@ -237,7 +267,7 @@ int oracle_warp_u8(const uint8_t *src, long H, long W, long C, const float *M,
         for (long x = 0; x < w; ++x) {
             float sx, sy;
             long out[3] = {0, 0, 0};
-            if (warp_coord(M, x, y, &sx, &sy)) {
+            if (coord_of(M, persp, x, y, &sx, &sy)) {
                 long x0, qx, y0, qy;
                 warp_weight(sx, &x0, &qx);
                 warp_weight(sy, &y0, &qy);
@@ -263,6 +293,18 @@ int oracle_warp_u8(const uint8_t *src, long H, long W, long C, const float *M,
     return ORACLE_OK;
 }
 
+int oracle_warp_u8(const uint8_t *src, long H, long W, long C, const float *M,
+                   uint8_t *dst, long h, long w, int gray, uint8_t *touched)
+{
+    return warp_u8_impl(src, H, W, C, M, 0, dst, h, w, gray, touched);
+}
+
+int oracle_warp_persp_u8(const uint8_t *src, long H, long W, long C, const float *M,
+                         uint8_t *dst, long h, long w, int gray, uint8_t *touched)
+{
+    return warp_u8_impl(src, H, W, C, M, 1, dst, h, w, gray, touched);
+}
+
 static double tap_f64(const uint8_t *src, long H, long W, long C, long y, long x, long c)
 {
     if (x < 0 || x >= W || y < 0 || y >= H) return 0.0;
@@ -270,13 +312,13 @@ static double tap_f64(const uint8_t *src, long H, long W, long C, long y, long x
 }
 
 /* ======================================================================== */
-/* Affine warp, f32 form in double. The coordinate is the fp32 value from   */
-/* warp_coord; the fraction s - floor(s) is taken exactly in double and not */
-/* quantised.                                                               */
+/* Affine or perspective warp, f32 form in double. The coordinate is the    */
+/* fp32 value from warp_coord / persp_coord; the fraction s - floor(s) is    */
+/* taken exactly in double and not quantised.                               */
 /* ======================================================================== */
-int oracle_warp_f64(const uint8_t *src, long H, long W, long C, const float *M,
-                    double *dst, long h, long w, int gray,
-                    const double *mean, const double *stdv, uint8_t *touched)
+static int warp_f64_impl(const uint8_t *src, long H, long W, long C, const float *M, int persp,
+                         double *dst, long h, long w, int gray,
+                         const double *mean, const double *stdv, uint8_t *touched)
 {
     if (H < 1 || W < 1 || h < 1 || w < 1 || (C != 1 && C != 3)) return ORACLE_BAD;
     if (gray && C != 3) return ORACLE_BAD;
@@ -285,7 +327,7 @@ int oracle_warp_f64(const uint8_t *src, long H, long W, long C, const float *M,
         for (long x = 0; x < w; ++x) {
             float sx, sy;
             double v[3] = {0.0, 0.0, 0.0};
-            if (warp_coord(M, x, y, &sx, &sy)) {
+            if (coord_of(M, persp, x, y, &sx, &sy)) {
                 double dsx = (double)sx, dsy = (double)sy;
                 double fx0 = floor(dsx), fy0 = floor(dsy);
                 double fx = dsx - fx0, fy = dsy - fy0;
@@ -314,6 +356,20 @@ int oracle_warp_f64(const uint8_t *src, long H, long W, long C, const float *M,
     return ORACLE_OK;
 }
 
+int oracle_warp_f64(const uint8_t *src, long H, long W, long C, const float *M,
+                    double *dst, long h, long w, int gray,
+                    const double *mean, const double *stdv, uint8_t *touched)
+{
+    return warp_f64_impl(src, H, W, C, M, 0, dst, h, w, gray, mean, stdv, touched);
+}
+
+int oracle_warp_persp_f64(const uint8_t *src, long H, long W, long C, const float *M,
+                          double *dst, long h, long w, int gray,
+                          const double *mean, const double *stdv, uint8_t *touched)
+{
+    return warp_f64_impl(src, H, W, C, M, 1, dst, h, w, gray, mean, stdv, touched);
+}
+
 /* ======================================================================== */
 /* Standalone RGB -> gray, u8 (Sec. IV-B gray_from_rgb: Image<u8,3> in,     */
 /* Image<u8,1> out of the same size).                                       */
@@ -335,6 +391,18 @@ int oracle_warp_point(const float *M, long x, long y, float *sx, float *sy,
                       long *x0, long *qx, long *y0, long *qy)
 {
     int ok = warp_coord(M, x, y, sx, sy);
+    if (ok) {
+        warp_weight(*sx, x0, qx);
+        warp_weight(*sy, y0, qy);
+    }
+    return ok;
+}
+
+/* The same for the perspective coordinate. */
+int oracle_persp_point(const float *M, long x, long y, float *sx, float *sy,
+                       long *x0, long *qx, long *y0, long *qy)
+{
+    int ok = persp_coord(M, x, y, sx, sy);
     if (ok) {
         warp_weight(*sx, x0, qx);
         warp_weight(*sy, y0, qy);

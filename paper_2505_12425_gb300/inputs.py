@@ -88,6 +88,32 @@ def random_inverse_affine(rng, H: int, W: int, h: int | None = None, w: int | No
     return Minv[:2, :].astype(np.float32)
 
 
+def random_inverse_homography(rng, H: int, W: int, h: int | None = None, w: int | None = None,
+                              tilt: float = 0.25) -> np.ndarray:
+    """A float32 3x3 destination->source map: the affine of random_inverse_affine followed by
+    a keystone tilt (the projective row (px, py, 1) with |px| W, |py| H up to `tilt`, applied
+    about the destination centre), inverted in float64 and scaled so that m22 = 1."""
+    h = H if h is None else h
+    w = W if w is None else w
+    theta = math.radians(rng.uniform(-30.0, 30.0))
+    s = rng.uniform(0.8, 1.2)
+    tx, ty = rng.uniform(-100.0, 100.0, size=2)
+    A = _forward_affine(theta, s, tx, ty, (W / 2.0, H / 2.0), (w / 2.0, h / 2.0))
+    px = rng.uniform(-tilt, tilt) / max(w, 1)
+    py = rng.uniform(-tilt, tilt) / max(h, 1)
+    C1 = np.array([[1, 0, -w / 2.0], [0, 1, -h / 2.0], [0, 0, 1]], dtype=np.float64)
+    P = np.array([[1, 0, 0], [0, 1, 0], [px, py, 1]], dtype=np.float64)
+    C2 = np.array([[1, 0, w / 2.0], [0, 1, h / 2.0], [0, 0, 1]], dtype=np.float64)
+    F = C2 @ P @ C1 @ A
+    Minv = np.linalg.inv(F)
+    return (Minv / Minv[2, 2]).astype(np.float32)
+
+
+def homographies(seed: int, n: int, H: int, W: int, tilt: float = 0.25) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return np.stack([random_inverse_homography(rng, H, W, tilt=tilt) for _ in range(n)])
+
+
 def warp_matrix(seed: int, H: int, W: int) -> np.ndarray:
     return random_inverse_affine(np.random.default_rng(seed), H, W)
 

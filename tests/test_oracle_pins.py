@@ -402,3 +402,95 @@ def test_flip_equals_the_warp_with_the_mirror_map():
     img = inputs.uniform_image(75, H, W, 3)
     M = np.array([[-1, 0, W], [0, 1, 0]], np.float32)
     np.testing.assert_array_equal(oracle.flip_h_u8(img), oracle.warp_u8(img, M, H, W))
+
+
+# ---------------------------------------------------------------------------
+# Perspective warp
+# ---------------------------------------------------------------------------
+def _brute_persp_point(M, x, y):
+    m = [f32(v) for v in np.asarray(M, np.float32).reshape(9)]
+    xc = round_f32(Fraction(x) + Fraction(1, 2))
+    yc = round_f32(Fraction(y) + Fraction(1, 2))
+    X = fmaf_exact(m[0], xc, fmaf_exact(m[1], yc, m[2]))
+    Y = fmaf_exact(m[3], xc, fmaf_exact(m[4], yc, m[5]))
+    Z = fmaf_exact(m[6], xc, fmaf_exact(m[7], yc, m[8]))
+    if not Z > 0:
+        return False, None, None, None, None, None, None
+    q = round_f32(1 / Z)
+    sx = sub_f32(round_f32(X * q), Fraction(1, 2))
+    sy = sub_f32(round_f32(Y * q), Fraction(1, 2))
+    if not (abs(sx) < 2 ** 22 and abs(sy) < 2 ** 22):
+        return False, sx, sy, None, None, None, None
+
+    def weight(s):
+        k0 = math.floor(s)
+        f = sub_f32(s, k0)
+        t = f * 2048
+        k = math.floor(t)
+        return k0, k + (1 if t - k >= Fraction(1, 2) else 0)
+
+    x0, qx = weight(sx)
+    y0, qy = weight(sy)
+    return True, sx, sy, x0, qx, y0, qy
+
+
+def _homographies():
+    rng = np.random.default_rng(78)
+    mats = [np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1]], np.float32),
+            np.array([[1, 0, 0], [0, 1, 0], [0.05, 0, 1]], np.float32),          # keystone in x
+            np.array([[1, 0, 0], [0, 1, 0], [-0.3, 0.2, 1]], np.float32)]        # a horizon inside
+    for _ in range(9):
+        mats.append(inputs.random_inverse_homography(rng, 8, 8, tilt=0.8))
+    return mats
+
+
+@pytest.mark.parametrize("k", range(12))
+def test_persp_brute_force_point_and_image(k):
+    M = _homographies()[k]
+    img = inputs.uniform_image(100 + k, 8, 8, 3)
+    exp = np.zeros((8, 8, 3), np.uint8)
+    for y in range(8):
+        for x in range(8):
+            ok, sx, sy, x0, qx, y0, qy = _brute_persp_point(M, x, y)
+            got = oracle.persp_point(M, x, y)
+            assert got[0] == ok
+            if sx is not None:
+                assert Fraction(got[1]) == sx and Fraction(got[2]) == sy
+            if not ok:
+                continue
+            assert got[3:] == (x0, qx, y0, qy)
+            for c in range(3):
+                def tap(yy, xx):
+                    return int(img[yy, xx, c]) if 0 <= xx < 8 and 0 <= yy < 8 else 0
+                v = Fraction(tap(y0, x0) * (2048 - qx) * (2048 - qy) + tap(y0, x0 + 1) * qx * (2048 - qy)
+                             + tap(y0 + 1, x0) * (2048 - qx) * qy + tap(y0 + 1, x0 + 1) * qx * qy, 2 ** 22)
+                exp[y, x, c] = math.floor(v + Fraction(1, 2))
+    np.testing.assert_array_equal(oracle.warp_persp_u8(img, M, 8, 8), exp)
+
+
+@pytest.mark.parametrize("k", range(6))
+def test_persp_with_affine_last_row_is_the_affine_warp(k):
+    A = _matrices()[4 + k]
+    M = np.vstack([A, [0, 0, 1]]).astype(np.float32)
+    img = inputs.noise_gradient_image(110 + k, 40, 56)
+    np.testing.assert_array_equal(oracle.warp_persp_u8(img, M, 33, 61), oracle.warp_u8(img, A, 33, 61))
+    np.testing.assert_array_equal(oracle.warp_persp_f64(img, M, 33, 61), oracle.warp_f64(img, A, 33, 61))
+
+
+def test_persp_is_invariant_to_power_of_two_scaling():
+    # X, Y, Z all scale exactly, q = 1/Z scales exactly, X*q does not change
+    img = inputs.noise_gradient_image(120, 50, 70)
+    M = inputs.random_inverse_homography(np.random.default_rng(121), 50, 70, tilt=0.6)
+    ref = oracle.warp_persp_u8(img, M, 50, 70)
+    for s in (0.25, 2.0, 8.0):
+        np.testing.assert_array_equal(oracle.warp_persp_u8(img, (M * s).astype(np.float32), 50, 70), ref)
+    # a negative scale puts every point behind the camera: all zeros
+    assert not oracle.warp_persp_u8(img, -M, 50, 70).any()
+
+
+def test_persp_f64_is_within_the_fixed_point_bound_of_u8():
+    img = inputs.noise_gradient_image(122, 60, 80)
+    M = inputs.random_inverse_homography(np.random.default_rng(123), 60, 80, tilt=0.5)
+    u8 = oracle.warp_persp_u8(img, M, 60, 80).astype(np.float64)
+    f = oracle.warp_persp_f64(img, M, 60, 80) * 255.0
+    assert np.abs(u8 - f).max() <= U8_BOUND
