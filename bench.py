@@ -307,20 +307,29 @@ def serving_compare(torch, kr, dev, rates=(2000, 5000, 10000, 20000, 40000, 8000
 
 def next_rows(torch, kr, dev, imgs_dev, peak, reps=50):
     """The widening rows on the same frames, each one launch over the batch: nearest-neighbour
-    resize -> 1280x720 and horizontal flip. Algorithmic bytes = output + distinct source pixels
-    read (nearest: distinct source rows x distinct source columns; flip: every pixel)."""
+    resize -> 1280x720, horizontal flip, perspective warp (per-frame homographies, u8).
+    Algorithmic bytes = output + distinct source pixels read (nearest: distinct source rows x
+    distinct source columns; flip: every pixel; perspective: the oracle's touched bitmaps)."""
     n, H, W, C = imgs_dev.shape
     lib = kr.load()
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     s = kr.image(imgs_dev)
+    P = np.ascontiguousarray(inputs.bench_homographies(n).reshape(-1), dtype=np.float32)
+    Pp = P.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    pp = kr.post()
     outs = {"resize_nearest_u8": torch.empty((n, RS_H, RS_W, C), dtype=torch.uint8, device=dev),
-            "flip_u8": torch.empty((n, H, W, C), dtype=torch.uint8, device=dev)}
+            "flip_u8": torch.empty((n, H, W, C), dtype=torch.uint8, device=dev),
+            "warp_persp_u8": torch.empty((n, H, W, C), dtype=torch.uint8, device=dev)}
     ds = {k: kr.image(v) for k, v in outs.items()}
     calls = {"resize_nearest_u8": lambda: lib.kr_resize_nearest(ctypes.byref(s), ctypes.byref(ds["resize_nearest_u8"]), st),
-             "flip_u8": lambda: lib.kr_flip_horizontal(ctypes.byref(s), ctypes.byref(ds["flip_u8"]), st)}
+             "flip_u8": lambda: lib.kr_flip_horizontal(ctypes.byref(s), ctypes.byref(ds["flip_u8"]), st),
+             "warp_persp_u8": lambda: lib.kr_warp_perspective(ctypes.byref(s), ctypes.byref(ds["warp_persp_u8"]), Pp,
+                                                              ctypes.byref(pp), st)}
     rows = len({((2 * y + 1) * H) // (2 * RS_H) for y in range(RS_H)})
     cols = len({((2 * x + 1) * W) // (2 * RS_W) for x in range(RS_W)})
-    alg = {"resize_nearest_u8": n * (RS_H * RS_W * C + rows * cols * C), "flip_u8": n * 2 * H * W * C}
+    touched = json.load(open(os.path.join(ROOT, "tests", "golden", "bench_touched.json")))["per_op"]
+    alg = {"resize_nearest_u8": n * (RS_H * RS_W * C + rows * cols * C), "flip_u8": n * 2 * H * W * C,
+           "warp_persp_u8": n * H * W * C + sum(touched["warp_persp_u8"]["touched_bytes"][:n])}
     res = {}
     for name, fn in calls.items():
         for _ in range(3):

@@ -133,6 +133,20 @@ kr_status kr_warp_affine(const kr_image_t *src, const kr_image_t *dst, const flo
                          const kr_post_t *post, kr_stream_t stream);
 
 /*
+ * Perspective warp (the projective generalisation of kr_warp_affine; the
+ * paper names geometric transforms, Sec. II-A, and prints no convention).
+ * M: HOST pointer to batch x 9 floats, row-major 3x3 per image, mapping
+ * destination pixel centres to source pixel centres in homogeneous
+ * coordinates: X, Y, Z = fmaf(m_r0, x + 0.5, fmaf(m_r1, y + 0.5, m_r2)),
+ * q = 1/Z, sx = X q - 0.5, sy = Y q - 0.5 (fp32, round to nearest). Where
+ * Z <= 0 the sample is zero; otherwise taps, weights, border, post and dst
+ * rules as for kr_warp_affine (with the last row (0, 0, 1) the results equal
+ * kr_warp_affine's bit for bit). Non-finite entries give KR_ERR_INVALID_ARG.
+ */
+kr_status kr_warp_perspective(const kr_image_t *src, const kr_image_t *dst, const float *M,
+                              const kr_post_t *post, kr_stream_t stream);
+
+/*
  * RGB -> gray (Sec. III "RGB to grayscale"; Sec. IV-B gray_from_rgb takes an
  * Image<u8,3> and a pre-allocated Image<u8,1> of the same size).
  * src: u8 HWC C = 3. dst: u8 HWC C = 1, same height, width and batch.

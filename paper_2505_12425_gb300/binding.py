@@ -96,6 +96,7 @@ def load():
         lib.kr_warp_affine.argtypes = [P(KrImage), P(KrImage), P(ctypes.c_float), P(KrPost), ctypes.c_void_p]
         lib.kr_rgb_to_gray.argtypes = [P(KrImage), P(KrImage), ctypes.c_void_p]
         lib.kr_resize_nearest.argtypes = [P(KrImage), P(KrImage), ctypes.c_void_p]
+        lib.kr_warp_perspective.argtypes = [P(KrImage), P(KrImage), P(ctypes.c_float), P(KrPost), ctypes.c_void_p]
         lib.kr_flip_horizontal.argtypes = [P(KrImage), P(KrImage), ctypes.c_void_p]
         lib.kr_batch_workspace_size.argtypes = [ctypes.c_int32]
         lib.kr_batch_workspace_size.restype = ctypes.c_size_t
@@ -117,7 +118,7 @@ def load():
         lib.kr_last_error.restype = ctypes.c_char_p
         lib.kr_shutdown.argtypes = []
         lib.kr_shutdown.restype = None
-        for f in ("kr_resize_bilinear", "kr_warp_affine", "kr_rgb_to_gray", "kr_resize_nearest",
+        for f in ("kr_resize_bilinear", "kr_warp_affine", "kr_warp_perspective", "kr_rgb_to_gray", "kr_resize_nearest",
                   "kr_flip_horizontal", "kr_batch_submit",
                   "kr_batch_submit_noalloc", "kr_serve_run", "kr_device_errors",
                   "kr_tile_config_shape", "kr_autotune_batch", "kr_autotune_save", "kr_autotune_load"):
@@ -203,11 +204,11 @@ def kr_resize_bilinear(src, dst, gray=False, mean=None, std=None, dst_layout="hw
            "kr_resize_bilinear")
 
 
-def _mats(M, n):
+def _mats(M, n, k=6):
     import numpy as np
     a = np.ascontiguousarray(np.asarray(M, dtype=np.float32).reshape(-1))
-    if a.size != 6 * n:
-        raise ValueError(f"need {n} 2x3 matrices, got {a.size / 6}")
+    if a.size != k * n:
+        raise ValueError(f"need {n} matrices of {k} floats, got {a.size / k}")
     return a
 
 
@@ -219,6 +220,16 @@ def kr_warp_affine(src, dst, M, gray=False, mean=None, std=None, dst_layout="hwc
     _check(lib.kr_warp_affine(ctypes.byref(s), ctypes.byref(d),
                               a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(p),
                               _stream(stream)), "kr_warp_affine")
+
+
+def kr_warp_perspective(src, dst, M, gray=False, mean=None, std=None, dst_layout="hwc", stream=None):
+    """Perspective warp (M: (N,) 3x3 destination->source maps) of u8 HWC `src` into `dst`."""
+    lib = load()
+    s, d, p = image(src), image(dst, dst_layout), post(gray, mean, std)
+    a = _mats(M, s.batch, 9)
+    _check(lib.kr_warp_perspective(ctypes.byref(s), ctypes.byref(d),
+                                   a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(p),
+                                   _stream(stream)), "kr_warp_perspective")
 
 
 def kr_rgb_to_gray(src, dst, stream=None):

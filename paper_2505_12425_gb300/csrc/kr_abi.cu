@@ -244,6 +244,24 @@ kr_status kr_warp_affine(const kr_image_t *src, const kr_image_t *dst, const flo
     return KR_OK;
 }
 
+kr_status kr_warp_perspective(const kr_image_t *src, const kr_image_t *dst, const float *M,
+                              const kr_post_t *post, kr_stream_t stream)
+{
+    if (!M) return KR_ERR_INVALID_ARG;
+    OpDesc d;
+    kr_status st = build_resample(OP_PERSP, src, dst, post, d);
+    if (st != KR_OK) return st;
+    for (int64_t i = 0; i < (int64_t)d.batch * 9; ++i)
+        if (!std::isfinite(M[i])) return KR_ERR_INVALID_ARG;
+    d.M = M;
+    cudaError_t e = launch_resample(d, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_last_error("kr_warp_perspective", e);
+        return KR_ERR_CUDA;
+    }
+    return KR_OK;
+}
+
 kr_status kr_rgb_to_gray(const kr_image_t *src, const kr_image_t *dst, kr_stream_t stream)
 {
     GrayDesc d;

@@ -38,7 +38,7 @@ namespace kr {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-enum { OP_RESIZE = 0, OP_WARP = 1 };
+enum { OP_RESIZE = 0, OP_WARP = 1, OP_PERSP = 2 };
 enum { OUT_U8 = 0, OUT_U8_GRAY = 1, OUT_F32 = 2, OUT_F32_GRAY = 3 };
 
 // One image of one resampling operation, pointers already at that image.
@@ -64,7 +64,7 @@ struct Job {
     const CUtensorMap *tout;  // destination map, box = one output tile; null = 128-bit stores
     int32_t zimg;             // image coordinate of this job in both maps
     unsigned *err;            // device error flags (bit 0: a bounded TMA wait ran out)
-    float M[6];           // destination -> source map (warp)
+    float M[9];           // destination -> source map (warp: 2x3; perspective: 3x3), row-major
     float scale[3];       // f32: out = v255 * scale[c] + bias[c]
     float bias[3];
 };
@@ -162,6 +162,31 @@ __device__ __forceinline__ bool warp_coord(const float *M, int x, int y, float &
     sx = __fsub_rn(__fmaf_rn(M[0], xc, __fmaf_rn(M[1], yc, M[2])), 0.5f);
     sy = __fsub_rn(__fmaf_rn(M[3], xc, __fmaf_rn(M[4], yc, M[5])), 0.5f);
     return fabsf(sx) < 4194304.f && fabsf(sy) < 4194304.f;
+}
+
+// Perspective coordinate: homogeneous X, Y, Z by fp32 fmas, q = 1/Z (rounded), s = X q - 1/2.
+// No source (false) where Z <= 0, or beyond |s| < 2^22. With the last row (0, 0, 1) this is
+// warp_coord bit for bit.
+__device__ __forceinline__ bool persp_coord(const float *M, int x, int y, float &sx, float &sy)
+{
+    const float xc = __fadd_rn((float)x, 0.5f);
+    const float yc = __fadd_rn((float)y, 0.5f);
+    const float X = __fmaf_rn(M[0], xc, __fmaf_rn(M[1], yc, M[2]));
+    const float Y = __fmaf_rn(M[3], xc, __fmaf_rn(M[4], yc, M[5]));
+    const float Z = __fmaf_rn(M[6], xc, __fmaf_rn(M[7], yc, M[8]));
+    if (!(Z > 0.f)) {
+        sx = sy = 0.f;
+        return false;
+    }
+    const float q = __frcp_rn(Z);
+    sx = __fsub_rn(__fmul_rn(X, q), 0.5f);
+    sy = __fsub_rn(__fmul_rn(Y, q), 0.5f);
+    return fabsf(sx) < 4194304.f && fabsf(sy) < 4194304.f;
+}
+
+template <int OP> __device__ __forceinline__ bool map_coord(const float *M, int x, int y, float &sx, float &sy)
+{
+    return OP == OP_PERSP ? persp_coord(M, x, y, sx, sy) : warp_coord(M, x, y, sx, sy);
 }
 
 // floor and 11-bit weight (round half up of 2048 * frac, frac = s - floor(s) in fp32).
@@ -339,6 +364,12 @@ __device__ __forceinline__ F2 f2_sub(F2 a, F2 b)
 {
     F2 r;
     asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b)
+{
+    F2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
     return r;
 }
 __device__ __forceinline__ F2 f2_fma(F2 a, F2 b, F2 c)
@@ -621,7 +652,9 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         const int cx = (lane & 1) ? tx0 + nx - 1 : tx0, cy = (lane & 2) ? ty0 + ny - 1 : ty0;
         float sx = 0.f, sy = 0.f;
         bool ok = true;
-        if (lane < 4) ok = warp_coord(J.M, cx, cy, sx, sy) && fabsf(sx) < 1048576.f && fabsf(sy) < 1048576.f;
+        // (perspective: Z is affine in the pixel position, so Z > 0 at the four corners means
+        // Z > 0 over the tile, and the tile maps onto the convex hull of its corners' images)
+        if (lane < 4) ok = map_coord<OP>(J.M, cx, cy, sx, sy) && fabsf(sx) < 1048576.f && fabsf(sy) < 1048576.f;
         float mnx = lane < 4 ? sx : 3.0e38f, mxx = lane < 4 ? sx : -3.0e38f;
         float mny = lane < 4 ? sy : 3.0e38f, mxy = lane < 4 ? sy : -3.0e38f;
 #pragma unroll
@@ -653,7 +686,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     const int fx0 = ti.fx0, fx1 = ti.fx1, fy0 = ti.fy0, fy1 = ti.fy1;
     const int rows = fy1 - fy0 + 1, cols = fx1 - fx0 + 1;
     const int srow = raw_row_bytes(max(cols, 1), CIN), sw = word_row(max(cols, 1));
-    const bool zero_tile = OP == OP_WARP && ti.zero != 0;
+    const bool zero_tile = OP != OP_RESIZE && ti.zero != 0;
     bool staged = !zero_tile && cols >= 1 && rows >= 1 && J.foot_budget > 0;
     const int bph = (fx0 * CIN) & 15;   // 16-byte phase of the box in every row of 16-byte aligned rows
     const bool mbar_ok = FRESH || ts.mbar_ok != 0;
@@ -773,7 +806,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             if (c0 >= e16) continue;
             uint8_t *dstp = raw + r * rstride + 16 * j;
             uintptr_t lo = ibeg, hi = iend;   // bytes that may be read
-            if (OP == OP_WARP) {
+            if (OP != OP_RESIZE) {
                 // warp boxes may cross the image border: only the row's own pixels are
                 // read, everything else is the zero border
                 const int yi = fy0 + r;
@@ -957,12 +990,20 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                     for (int r = r0 + warp; r < r1; r += kWarps) {
                         const float yc = __fadd_rn((float)(ty0 + r), 0.5f);
                         const F2 rxy = f2_fma(my, f2_pack(yc, yc), m2);
+                        const float rz = OP == OP_PERSP ? __fmaf_rn(J.M[7], yc, J.M[8]) : 0.f;
                         const ORow o = orow_of(r);
 #pragma unroll
                         for (int j = 0; j < CPL; ++j) {
                             const int c = lane + 32 * j;
                             if (c < nx) {
-                                const F2 a2 = f2_fma(mx, xc2[j], rxy);
+                                F2 a2 = f2_fma(mx, xc2[j], rxy);
+                                if (OP == OP_PERSP) {
+                                    // (X, Y) q with q = 1/Z: Z > 0 over the tile (its corners)
+                                    float xc, xc_hi;
+                                    f2_unpack(xc2[j], xc, xc_hi);
+                                    const float q = __frcp_rn(__fmaf_rn(J.M[6], xc, rz));
+                                    a2 = f2_mul(a2, f2_pack(q, q));
+                                }
                                 uint32_t xi, yi;
                                 int qx = 0, qy = 0;
                                 float fx = 0.f, fy = 0.f;
@@ -994,7 +1035,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                 }
             };
             if (rawbox) fast3(IntC<TAPS_RAW>{}); else fast3(IntC<TAPS_WORDS>{});
-        } else if (OP == OP_WARP && CIN == 3 && staged) {
+        } else if (OP != OP_RESIZE && CIN == 3 && staged) {
             // Medium path (warp tiles with coordinates outside [0, 4094)): the exact weight
             // formula per pixel; every tap still lies in the zero-filled box.
             auto medium3 = [&](auto fmt) {
@@ -1008,9 +1049,14 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                     for (int j = 0; j < CPL; ++j) {
                         const int c = lane + 32 * j;
                         if (c < nx) {
-                            const float xc = __fadd_rn((float)(tx0 + c), 0.5f);
-                            const float sx = __fsub_rn(__fmaf_rn(J.M[0], xc, rx), 0.5f);
-                            const float sy = __fsub_rn(__fmaf_rn(J.M[3], xc, ry), 0.5f);
+                            float sx, sy;
+                            if (OP == OP_PERSP) {
+                                persp_coord(J.M, tx0 + c, ty0 + r, sx, sy);   // valid: Z > 0 over the tile
+                            } else {
+                                const float xc = __fadd_rn((float)(tx0 + c), 0.5f);
+                                sx = __fsub_rn(__fmaf_rn(J.M[0], xc, rx), 0.5f);
+                                sy = __fsub_rn(__fmaf_rn(J.M[3], xc, ry), 0.5f);
+                            }
                             int x0, y0, qx, qy;
                             warp_weight(sx, x0, qx);
                             warp_weight(sy, y0, qy);
@@ -1055,7 +1101,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                         y0 = ts.ry0[r]; dy = ts.rqd[r] >> 16; qy = ts.rqd[r] & 0xFFFF; fy = ts.rf[r];
                     } else {
                         float sx, sy;
-                        valid = warp_coord(J.M, x, y, sx, sy);
+                        valid = map_coord<OP>(J.M, x, y, sx, sy);
                         if (valid) {
                             warp_weight(sx, x0, qx);
                             warp_weight(sy, y0, qy);

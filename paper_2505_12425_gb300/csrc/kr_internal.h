@@ -20,7 +20,7 @@ constexpr int kRegionBCap = 34 * 1024;
 
 // A validated single-image-op request, pointers as device addresses.
 struct OpDesc {
-    int op;          // OP_RESIZE / OP_WARP
+    int op;          // OP_RESIZE / OP_WARP / OP_PERSP
     int cin;         // source channels (1 or 3)
     int outk;        // OUT_U8 / OUT_U8_GRAY / OUT_F32 / OUT_F32_GRAY
     const uint8_t *src;
@@ -32,7 +32,7 @@ struct OpDesc {
     int chw;
     int batch;
     float scale[3], bias[3];
-    const float *M;  // host, 6 * batch floats (warp)
+    const float *M;  // host, 6 * batch floats (warp) or 9 * batch (perspective)
 };
 
 // Per-op launch (per-image tiles, blockIdx.z = image). Returns cudaSuccess or the launch error.
@@ -74,6 +74,7 @@ struct Budget {
 };
 Budget budget_resize(int cin, int H, int W, int h, int w, int tw, int th, int out_bytes);
 Budget budget_warp(int cin, int H, int W, const float *M, int tw, int th, int out_bytes);
+Budget budget_persp(int cin, int H, int W, const float *M, int h, int w, int tw, int th, int out_bytes);
 // Warp maps whose terms |m00| w, |m01| h, |m02| (and the second row) stay below 2^19 keep
 // every intermediate of the fp32 coordinate below 2^20, so interior pixels deviate from the
 // corner hull by far less than the box margin: such maps may use the fast tile path.

@@ -20,6 +20,9 @@ constexpr int kTH = 32;
 // Device error flags of the per-operation kernels (bit 0: a bounded TMA wait ran out).
 static __device__ unsigned g_kr_device_err;
 
+// Largest raw box (bytes of 16-byte chunk rows) a 3-channel launch stages.
+constexpr long long kRawBoxCap = 56 * 1024;
+
 struct OpParams {
     CUtensorMap tin;    // source map (valid when has_tin)
     CUtensorMap tout;   // destination map (valid when has_tout)
@@ -38,7 +41,7 @@ struct OpParams {
     int32_t rows16;
     uint32_t fast_mask[(kMaxMPerLaunch + 31) / 32];   // warp: images whose map allows the fast path
     float scale[3], bias[3];
-    float M[kMaxMPerLaunch][6];
+    float M[kMaxMPerLaunch][9];   // warp: 6 floats per image; perspective: 9
 };
 
 // ROWS: instantiated for launches whose 3-channel boxes are staged by bulk row copies (no
@@ -64,7 +67,7 @@ __global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constan
     J.region_b = p.region_b;
     J.raw_taps = p.raw_taps;
     J.rows16 = p.rows16;
-    J.allow_fast = OP == OP_WARP ? (int)((p.fast_mask[z >> 5] >> (z & 31)) & 1u) : 1;
+    J.allow_fast = OP != OP_RESIZE ? (int)((p.fast_mask[z >> 5] >> (z & 31)) & 1u) : 1;
     J.tin = p.has_tin ? &p.tin : nullptr;
     J.tin_nc = p.tin_nc;
     J.tin_br = p.tin_br;
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constan
     J.zimg = z;
     J.err = &g_kr_device_err;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) J.M[k] = OP == OP_WARP ? p.M[z][k] : 0.f;
+    for (int k = 0; k < 9; ++k) J.M[k] = OP != OP_RESIZE ? p.M[z][k] : 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         J.scale[k] = p.scale[k];
@@ -132,6 +135,46 @@ Budget budget_warp(int cin, int H, int W, const float *M, int tw, int th, int ou
     const double cols = std::ceil(std::fabs(M[0]) * (tw - 1) + std::fabs(M[1]) * (th - 1)) + 6;
     const double rows = std::ceil(std::fabs(M[3]) * (tw - 1) + std::fabs(M[4]) * (th - 1)) + 6;
     if (!(cols < 1e7 && rows < 1e7)) return budget_for(cin, 1e7, 1e7, H, W, out_bytes, true);
+    return budget_for(cin, cols, rows, H, W, out_bytes, true);
+}
+
+Budget budget_persp(int cin, int H, int W, const float *M, int h, int w, int tw, int th, int out_bytes)
+{
+    // The box of a tile is the hull of its corners' images (Z > 0 at the corners); its size
+    // varies over the output. The bound is taken on a grid of cells of k x k tiles (k keeps
+    // the grid near 16 x 16 cells: the launch stays cheap on the host) over the cells whose
+    // corners map in front of the camera: a cell's box / k, 15% and six pixels of margin.
+    // It only sizes the staging: a tile whose box is larger takes the general path.
+    const int tiles_x = (w + tw - 1) / tw, tiles_y = (h + th - 1) / th;
+    const int k = std::max(1, (int)std::ceil(std::sqrt((double)tiles_x * tiles_y / 256.0)));
+    double cols = 0, rows = 0;
+    auto at = [&](double x, double y, double &sx, double &sy) {
+        const double xc = x + 0.5, yc = y + 0.5;
+        const double Z = M[6] * xc + M[7] * yc + M[8];
+        if (!(Z > 0)) return false;
+        sx = (M[0] * xc + M[1] * yc + M[2]) / Z - 0.5;
+        sy = (M[3] * xc + M[4] * yc + M[5]) / Z - 0.5;
+        return std::fabs(sx) < 1048576.0 && std::fabs(sy) < 1048576.0;
+    };
+    for (int cy = 0; cy < tiles_y; cy += k)
+        for (int cx = 0; cx < tiles_x; cx += k) {
+            const int x0 = cx * tw, y0 = cy * th;
+            const int x1 = std::min(w, (cx + k) * tw) - 1, y1 = std::min(h, (cy + k) * th) - 1;
+            const int kx = std::min(k, tiles_x - cx), ky = std::min(k, tiles_y - cy);
+            double sx[4], sy[4];
+            if (!at(x0, y0, sx[0], sy[0]) || !at(x1, y0, sx[1], sy[1]) || !at(x0, y1, sx[2], sy[2]) ||
+                !at(x1, y1, sx[3], sy[3]))
+                continue;
+            const double bw = std::max(std::max(sx[0], sx[1]), std::max(sx[2], sx[3])) -
+                              std::min(std::min(sx[0], sx[1]), std::min(sx[2], sx[3]));
+            const double bh = std::max(std::max(sy[0], sy[1]), std::max(sy[2], sy[3])) -
+                              std::min(std::min(sy[0], sy[1]), std::min(sy[2], sy[3]));
+            // a k x k cell's box over k tiles of each side (the box is linear in the side)
+            const double scale = std::max(kx, ky) > 1 ? 1.15 / std::max(kx, ky) : 1.0;
+            cols = std::max(cols, std::ceil(bw * scale) + 6);
+            rows = std::max(rows, std::ceil(bh * scale) + 6);
+        }
+    if (cols == 0 || !(cols < 1e7 && rows < 1e7)) return budget_for(cin, 1e7, 1e7, H, W, out_bytes, true);
     return budget_for(cin, cols, rows, H, W, out_bytes, true);
 }
 
@@ -236,62 +279,72 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
         p.bias[k] = d.bias[k];
     }
     const int tiles_x = (d.w + TW - 1) / TW, tiles_y = (d.h + TH - 1) / TH;
-    const int per_launch = OP == OP_WARP ? kMaxMPerLaunch : 65535;
+    const int per_launch = OP != OP_RESIZE ? kMaxMPerLaunch : 65535;
+    constexpr int nm = OP == OP_PERSP ? 9 : 6;   // floats per image map
     for (int b0 = 0; b0 < d.batch; b0 += per_launch) {
         const int nb = std::min(per_launch, d.batch - b0);
         constexpr int ob = out_stage_bytes<OUTK, CIN, TW, TH>();
         Budget bud;
         std::memset(p.fast_mask, 0, sizeof(p.fast_mask));
+        // Raw-tap box bound (3 channels): the largest tile box of the launch whose raw rows
+        // (16-byte chunks) fit kRawBoxCap; it is independent of the re-laid layout's caps.
+        int raw_cols = 0, raw_rows = 0;
+        auto raw_bound = [&](const Budget &bi) {
+            if (CIN != 3 || bi.cols < 1 || bi.rows < 1 || bi.cols >= 1000000) return;
+            const long long raw = 16LL * ((15 + bi.cols * CIN + 15) / 16) * bi.rows + 16;
+            if (raw > kRawBoxCap) return;
+            raw_cols = std::max(raw_cols, bi.cols);
+            raw_rows = std::max(raw_rows, bi.rows);
+        };
         if (OP == OP_RESIZE) {
             bud = budget_resize(CIN, d.H, d.W, d.h, d.w, TW, TH, ob);
+            raw_bound(bud);
         } else {
             bud.a = 0;
             bud.b = round16(ob);
             for (int i = 0; i < nb; ++i) {
-                for (int k = 0; k < 6; ++k) p.M[i][k] = d.M[(size_t)(b0 + i) * 6 + k];
-                const Budget bi = budget_warp(CIN, d.H, d.W, p.M[i], TW, TH, ob);
+                for (int k = 0; k < nm; ++k) p.M[i][k] = d.M[(size_t)(b0 + i) * nm + k];
+                const Budget bi = OP == OP_PERSP ? budget_persp(CIN, d.H, d.W, p.M[i], d.h, d.w, TW, TH, ob)
+                                                 : budget_warp(CIN, d.H, d.W, p.M[i], TW, TH, ob);
                 bud.a = std::max(bud.a, bi.a);
                 bud.b = std::max(bud.b, bi.b);
                 if (bi.fits) {   // the TMA box covers every image whose tiles' boxes fit the caps
                     bud.cols = std::max(bud.cols, bi.cols);
                     bud.rows = std::max(bud.rows, bi.rows);
                 }
+                raw_bound(bi);
                 if (warp_allows_fast(p.M[i], d.h, d.w)) p.fast_mask[i >> 5] |= 1u << (i & 31);
             }
         }
         p.src = d.src + (int64_t)b0 * d.sbatch;
         p.dst = d.dst + (int64_t)b0 * d.dbatch;
-        // TMA source map: one box per tile covering the largest source box of the launch
         p.has_tin = 0;
         p.raw_taps = 0;
         p.rows16 = ((uintptr_t)p.src & 15) == 0 && (d.spitch & 15) == 0 && (nb == 1 || (d.sbatch & 15) == 0);
-        if (bud.a > 0 && bud.cols > 0 && bud.rows > 0) {
+        if (CIN == 3 && raw_cols > 0) {
+            // 3-channel taps straight from the staged rows: region A holds the largest raw box
+            // plus the 16 bytes that reading the last pixel pair may touch past it, region B
+            // only the output tile; the rows come by one TMA copy per tile when the source
+            // takes a map, else by bulk row copies when its rows are 16-byte aligned
+            const int nc = (15 + raw_cols * CIN + 15) / 16, br = raw_rows;
+            if (encode_map(&p.tin, p.src, (int64_t)d.W * CIN, d.H, 1, nb, d.spitch, 0, d.sbatch, nc, br)) {
+                p.has_tin = 1;
+                p.tin_nc = nc;
+                p.tin_br = br;
+            }
+            if (p.has_tin || p.rows16) {
+                p.raw_taps = 1;
+                bud.a = round128(16 * nc * br + 16);
+                bud.b = round16(ob);
+            }
+        } else if (CIN == 1 && bud.a > 0 && bud.cols > 0 && bud.rows > 0) {
+            // TMA source map: one box per tile covering the largest source box of the launch
             const int nc = (15 + bud.cols * CIN + 15) / 16, br = bud.rows;
-            const long long cap = CIN == 3 ? bud.b : bud.a - 16;
-            if ((long long)16 * nc * br <= cap &&
+            if ((long long)16 * nc * br <= bud.a - 16 &&
                 encode_map(&p.tin, p.src, (int64_t)d.W * CIN, d.H, 1, nb, d.spitch, 0, d.sbatch, nc, br)) {
                 p.has_tin = 1;
                 p.tin_nc = nc;
                 p.tin_br = br;
-                if (CIN == 3) {
-                    // 3-channel taps straight from the staged rows: region A holds the map's
-                    // box plus the 16 bytes that reading the last pixel pair may touch past
-                    // it, region B only the output tile
-                    p.raw_taps = 1;
-                    bud.a = round128(16 * nc * br + 16);
-                    bud.b = round16(ob);
-                }
-            }
-        }
-        if (CIN == 3 && !p.has_tin && p.rows16 && bud.a > 0 && bud.cols > 0 && bud.rows > 0) {
-            // no map, but 16-byte aligned rows: bulk row copies and raw taps, region A sized
-            // for the largest box (plus the 16 bytes a last pixel pair may touch)
-            const int nc = (15 + bud.cols * CIN + 15) / 16;
-            const long long a = 16LL * nc * bud.rows + 16;
-            if (a <= std::max<long long>(bud.b, kRegionBCap)) {
-                p.raw_taps = 1;
-                bud.a = round128((int)a);
-                bud.b = round16(ob);
             }
         }
         p.foot_budget = bud.a;
@@ -339,7 +392,9 @@ static cudaError_t launch_op(const OpDesc &d, cudaStream_t s)
 
 cudaError_t launch_resample(const OpDesc &d, cudaStream_t stream)
 {
-    return d.op == OP_RESIZE ? launch_op<OP_RESIZE>(d, stream) : launch_op<OP_WARP>(d, stream);
+    if (d.op == OP_RESIZE) return launch_op<OP_RESIZE>(d, stream);
+    if (d.op == OP_PERSP) return launch_op<OP_PERSP>(d, stream);
+    return launch_op<OP_WARP>(d, stream);
 }
 
 // ---------------------------------------------------------------------------

@@ -138,6 +138,12 @@ def bench_matrices(n: int = BENCH_IMAGES) -> np.ndarray:
     return np.stack([warp_matrix(3000 + i, BENCH_H, BENCH_W) for i in range(n)])
 
 
+def bench_homographies(n: int = BENCH_IMAGES, tilt: float = 0.25) -> np.ndarray:
+    """Per-frame 3x3 inverse maps of the perspective row (seeds 3500 + i)."""
+    return np.stack([random_inverse_homography(np.random.default_rng(3500 + i), BENCH_H, BENCH_W, tilt=tilt)
+                     for i in range(n)])
+
+
 @dataclass
 class RaggedItem:
     op: int

@@ -25,6 +25,7 @@ def main():
     n, H, W = inputs.BENCH_IMAGES, inputs.BENCH_H, inputs.BENCH_W
     imgs = inputs.bench_images(n)
     Ms = inputs.bench_matrices(n)
+    Ps = inputs.bench_homographies(n)
     pitch = W * 3
     acc = {}
 
@@ -48,8 +49,10 @@ def main():
             add(op, w8)
         add("warp_f32", wf)
         add("rgb_to_gray", np.ones((H, W), np.uint8))
+        _, p8 = oracle.warp_persp_u8(imgs[i], Ps[i], H, W, touched=True)
+        add("warp_persp_u8", p8)
     out = {
-        "workload": f"{n} x {W}x{H}x3 u8 noise+gradient frames (inputs.bench_images / bench_matrices)",
+        "workload": f"{n} x {W}x{H}x3 u8 noise+gradient frames (inputs.bench_images / bench_matrices / bench_homographies)",
         "images": n,
         "per_image": "lists hold one value per frame, frame i = bench_images()[i]",
         "per_op": {k: {"touched_bytes": v[0], "touched_sector_bytes": v[1]} for k, v in sorted(acc.items())},

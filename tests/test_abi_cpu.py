@@ -98,6 +98,18 @@ def test_warp_rejects_nonfinite_matrix(lib):
     assert lib.kr_warp_affine(ctypes.byref(s), ctypes.byref(d), None, ctypes.byref(p), None) == 1
 
 
+def test_perspective_rejects_bad_maps(lib):
+    s, d, p = _img(), _img(data=0x900000), kr.KrPost()
+    assert lib.kr_warp_perspective(ctypes.byref(s), ctypes.byref(d), None, ctypes.byref(p), None) == 1
+    for k in (0, 5, 8):
+        M = [1, 0, 0, 0, 1, 0, 0, 0, 1]
+        M[k] = float("nan")
+        a = (ctypes.c_float * 9)(*M)
+        assert lib.kr_warp_perspective(ctypes.byref(s), ctypes.byref(d), a, ctypes.byref(p), None) == 1
+    a = (ctypes.c_float * 9)(1, 0, 0, 0, 1, 0, 0, 0, 1)
+    assert lib.kr_warp_perspective(ctypes.byref(s), ctypes.byref(_img(data=0x10001)), a, ctypes.byref(p), None) == 3
+
+
 def test_gathers_reject_bad_shapes(lib):
     s = _img()
     for f in (lib.kr_resize_nearest, lib.kr_flip_horizontal):

@@ -408,3 +408,71 @@ def test_flip_equals_warp_with_the_mirror_map():
     kr.kr_warp_affine(to_dev(img), w, M)
     torch.cuda.synchronize()
     assert torch.equal(f, w)
+
+
+# ---------------------------------------------------------------------------
+# Perspective warp
+# ---------------------------------------------------------------------------
+PERSP_CASES = [(1080, 1920, 3, 0.25, 30), (99, 160, 3, 0.8, 31), (71, 90, 1, 0.5, 32), (64, 96, 3, 1.5, 33),
+               (257, 129, 3, 2.5, 34)]   # the last ones put a horizon inside the output
+
+
+@pytest.mark.parametrize("H,W,C,tilt,seed", PERSP_CASES)
+def test_warp_perspective_u8(H, W, C, tilt, seed):
+    img = inputs.noise_gradient_image(seed, H, W, C)
+    M = inputs.random_inverse_homography(np.random.default_rng(seed), H, W, tilt=tilt)
+    out = Guarded((H, W, C), torch.uint8)
+    kr.kr_warp_perspective(to_dev(img), out.t, M)
+    torch.cuda.synchronize()
+    out.check()
+    np.testing.assert_array_equal(out.np(), oracle.warp_persp_u8(img, M, H, W))
+
+
+@pytest.mark.parametrize("layout", ["hwc", "chw"])
+@pytest.mark.parametrize("H,W,tilt,seed", [(1080, 1920, 0.25, 40), (83, 121, 1.2, 41)])
+def test_warp_perspective_f32(H, W, tilt, seed, layout):
+    img = inputs.noise_gradient_image(seed, H, W)
+    M = inputs.random_inverse_homography(np.random.default_rng(seed), H, W, tilt=tilt)
+    shape = (H, W, 3) if layout == "hwc" else (3, H, W)
+    out = Guarded(shape, torch.float32)
+    kr.kr_warp_perspective(to_dev(img), out.t, M, mean=MEAN, std=STD, dst_layout=layout)
+    g = Guarded((H, W, 1), torch.uint8)
+    kr.kr_warp_perspective(to_dev(img), g.t, M, gray=True)
+    torch.cuda.synchronize()
+    out.check()
+    g.check()
+    got = out.np() if layout == "hwc" else out.np().transpose(1, 2, 0)
+    assert np.abs(got - oracle.warp_persp_f64(img, M, H, W, mean=MEAN, std=STD)).max() <= F32_TOL
+    np.testing.assert_array_equal(g.np(), oracle.warp_persp_u8(img, M, H, W, gray=True))
+
+
+def test_perspective_with_affine_last_row_equals_affine_warp():
+    n, H, W = 4, 1080, 1920
+    imgs = inputs.bench_images(n)
+    A = inputs.bench_matrices(n)
+    P = np.concatenate([A.reshape(n, 2, 3), np.tile(np.array([[[0, 0, 1]]], np.float32), (n, 1, 1))], axis=1)
+    src = to_dev(imgs)
+    a = torch.empty((n, H, W, 3), dtype=torch.uint8, device=dev())
+    p = torch.empty_like(a)
+    kr.kr_warp_affine(src, a, A)
+    kr.kr_warp_perspective(src, p, P)
+    af = torch.empty((n, H, W, 3), dtype=torch.float32, device=dev())
+    pf = torch.empty_like(af)
+    kr.kr_warp_affine(src, af, A)
+    kr.kr_warp_perspective(src, pf, P)
+    torch.cuda.synchronize()
+    assert torch.equal(a, p)
+    assert torch.equal(af, pf)
+
+
+def test_perspective_behind_the_camera_is_the_zero_sample():
+    H, W = 50, 70
+    img = inputs.uniform_image(44, H, W, 3)
+    M = -np.eye(3, dtype=np.float32)                   # Z = -1 everywhere
+    u = Guarded((H, W, 3), torch.uint8)
+    f = Guarded((H, W, 3), torch.float32)
+    kr.kr_warp_perspective(to_dev(img), u.t, M)
+    kr.kr_warp_perspective(to_dev(img), f.t, M, mean=MEAN, std=STD)
+    torch.cuda.synchronize()
+    assert not u.np().any()
+    np.testing.assert_allclose(f.np(), np.broadcast_to(-np.array(MEAN) / np.array(STD), (H, W, 3)), atol=1e-6)
