@@ -67,6 +67,7 @@ def _load():
                                                   _f64p, _f64p, _u8p]
             lib.oracle_persp_point.argtypes = [_f32p, _L, _L, _f32p, _f32p, _lp, _lp, _lp, _lp]
             lib.oracle_flip_h_u8.argtypes = [_u8p, _L, _L, _L, _u8p]
+            lib.oracle_sobel.argtypes = [_u8p, _L, _L, _L, _f32p, _u8p]
             for f in (lib.oracle_resize_u8, lib.oracle_resize_f64, lib.oracle_warp_u8,
                       lib.oracle_warp_f64, lib.oracle_rgb_to_gray_u8, lib.oracle_warp_point,
                       lib.oracle_resize_point):
@@ -182,6 +183,19 @@ def resize_nearest_u8(img, h, w):
     if rc != 0:
         raise ValueError("oracle_resize_nearest_u8: bad arguments")
     return out
+
+
+def sobel(img):
+    """Sobel 3x3 magnitude (replicated border, normalised kernels) of an H x W x C u8 image
+    (C = 3: of its u8 gray): (f32 H x W x 1, u8 H x W x 1)."""
+    src = _src(img)
+    H, W, C = src.shape
+    f = np.zeros((H, W, 1), dtype=np.float32)
+    u = np.zeros((H, W, 1), dtype=np.uint8)
+    rc = _load().oracle_sobel(_p(src, _u8p), H, W, C, _p(f, _f32p), _p(u, _u8p))
+    if rc != 0:
+        raise ValueError("oracle_sobel: bad arguments")
+    return f, u
 
 
 def flip_h_u8(img):

@@ -18,7 +18,9 @@
  *     neighbor resizing") and horizontal flip (Sec. IV-A, Rust benchmark);
  *   - perspective warp with a 3x3 inverse map (the projective generalisation
  *     of the affine warp; Sec. II-A "geometric transforms"), same taps,
- *     weights and border as the affine warp.
+ *     weights and border as the affine warp;
+ *   - Sobel 3x3 gradient magnitude (Sec. V: the robotics example's
+ *     imgproc::filter::sobel(&img, &mut out, 3), RGB8 in, Gray8 out).
  *
  * The paper prints none of the arithmetic. The conventions used here are:
  *   half-pixel centres; resize clamps to the edge; warp reads zero outside the
@@ -452,5 +454,44 @@ int oracle_flip_h_u8(const uint8_t *src, long H, long W, long C, uint8_t *dst)
         for (long x = 0; x < W; ++x)
             for (long c = 0; c < C; ++c)
                 dst[(y * W + x) * C + c] = src[(y * W + (W - 1 - x)) * C + c];
+    return ORACLE_OK;
+}
+
+/* ======================================================================== */
+/* Sobel 3x3 gradient magnitude (Sec. V example: kernel size 3, an RGB8     */
+/* image in and a Gray8 image out; the paper gives no formula). Readings:   */
+/* a 3-channel source is first the u8 BT.601 gray above; the border         */
+/* replicates the edge pixel; with                                          */
+/*   gx = sum_{dy,dx} (dx (2 - |dy|)) I(y + dy, x + dx),                    */
+/*   gy = sum_{dy,dx} (dy (2 - |dx|)) I(y + dy, x + dx),                    */
+/* (the Sobel kernels [-1 0 1; -2 0 2; -1 0 1] and their transpose, both    */
+/* integers) the f32 output is the magnitude of the normalised kernels      */
+/*   m = sqrtf((float)(gx*gx + gy*gy)) / 8     (exact up to the one sqrt     */
+/*                                              rounding: gx^2 + gy^2 < 2^24) */
+/* and the u8 output is floorf(m + 0.5f) (at most 181).                     */
+/* Either output pointer may be NULL.                                       */
+/* ======================================================================== */
+static long clampl(long v, long lo, long hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+int oracle_sobel(const uint8_t *src, long H, long W, long C, float *out_f32, uint8_t *out_u8)
+{
+    if (H < 1 || W < 1 || (C != 1 && C != 3)) return ORACLE_BAD;
+    for (long y = 0; y < H; ++y) {
+        for (long x = 0; x < W; ++x) {
+            long gx = 0, gy = 0;
+            for (long dy = -1; dy <= 1; ++dy) {
+                for (long dx = -1; dx <= 1; ++dx) {
+                    const long yy = clampl(y + dy, 0, H - 1), xx = clampl(x + dx, 0, W - 1);
+                    const uint8_t *p = src + (yy * W + xx) * C;
+                    const long v = C == 3 ? gray_u8(p[0], p[1], p[2]) : p[0];
+                    gx += dx * (2 - (dy < 0 ? -dy : dy)) * v;
+                    gy += dy * (2 - (dx < 0 ? -dx : dx)) * v;
+                }
+            }
+            const float m = sqrtf((float)(gx * gx + gy * gy)) / 8.0f;
+            if (out_f32) out_f32[y * W + x] = m;
+            if (out_u8) out_u8[y * W + x] = (uint8_t)floorf(m + 0.5f);
+        }
+    }
     return ORACLE_OK;
 }

@@ -494,3 +494,45 @@ def test_persp_f64_is_within_the_fixed_point_bound_of_u8():
     u8 = oracle.warp_persp_u8(img, M, 60, 80).astype(np.float64)
     f = oracle.warp_persp_f64(img, M, 60, 80) * 255.0
     assert np.abs(u8 - f).max() <= U8_BOUND
+
+
+# ---------------------------------------------------------------------------
+# Sobel 3x3
+# ---------------------------------------------------------------------------
+def test_sobel_of_a_constant_image_is_zero():
+    f, u = oracle.sobel(np.full((9, 11, 3), 77, np.uint8))
+    assert not f.any() and not u.any()
+
+
+def test_sobel_of_a_ramp():
+    # I = 3x: interior gx = (1 + 2 + 1) * (I(x+1) - I(x-1)) = 4 * 6 = 24 -> 24 / 8 = 3;
+    # at the replicated edges the difference is one step: 4 * 3 / 8 = 1.5
+    W = 12
+    img = np.tile((3 * np.arange(W, dtype=np.uint8))[None, :, None], (7, 1, 1))
+    f, u = oracle.sobel(img)
+    np.testing.assert_array_equal(f[:, 1:-1, 0], 3.0)
+    np.testing.assert_array_equal(f[:, [0, -1], 0], 1.5)
+    np.testing.assert_array_equal(u[:, [0, -1], 0], 2)          # floor(1.5 + 0.5)
+
+
+def test_sobel_matches_scipy_with_nearest_mode():
+    ndimage = pytest.importorskip("scipy.ndimage")
+    img = inputs.uniform_image(130, 31, 47, 1)
+    f, u = oracle.sobel(img)
+    g = img[..., 0].astype(np.float64)
+    sx = ndimage.sobel(g, axis=1, mode="nearest")
+    sy = ndimage.sobel(g, axis=0, mode="nearest")
+    ref = np.hypot(sx, sy) / 8.0
+    np.testing.assert_allclose(f[..., 0], ref, rtol=1e-6, atol=1e-6)
+    away = np.abs(ref - np.floor(ref) - 0.5) > 1e-3                  # not at a rounding tie
+    np.testing.assert_array_equal(u[..., 0][away], np.floor(ref + 0.5)[away])
+
+
+def test_sobel_commutes_with_transpose_and_fuses_gray():
+    img = inputs.noise_gradient_image(131, 23, 29)
+    f, u = oracle.sobel(img)
+    g = oracle.rgb_to_gray_u8(img)
+    fg, ug = oracle.sobel(g)
+    np.testing.assert_array_equal(f, fg)
+    ft, _ = oracle.sobel(np.ascontiguousarray(g.transpose(1, 0, 2)))
+    np.testing.assert_array_equal(ft, f.transpose(1, 0, 2))
