@@ -170,6 +170,18 @@ kr_status kr_resize_nearest(const kr_image_t *src, const kr_image_t *dst, kr_str
  */
 kr_status kr_flip_horizontal(const kr_image_t *src, const kr_image_t *dst, kr_stream_t stream);
 
+/*
+ * Sobel gradient magnitude (Sec. V: the robotics example calls
+ * imgproc::filter::sobel(&img, &mut out, 3) on an RGB8 image into a Gray8
+ * image; the paper gives no formula). ksize must be 3 (KR_ERR_UNSUPPORTED
+ * otherwise). src: u8 HWC, C = 1, or C = 3 (first the u8 BT.601 gray of
+ * kr_rgb_to_gray). Border: the edge pixel is replicated. With the integer
+ * Sobel sums gx, gy of [-1 0 1; -2 0 2; -1 0 1] and its transpose,
+ * m = sqrt(gx^2 + gy^2) / 8 (fp32, one rounding of the square root);
+ * dst: C = 1, same size and batch, f32 (m) or u8 (floor(m + 1/2), <= 181).
+ */
+kr_status kr_sobel(const kr_image_t *src, const kr_image_t *dst, int32_t ksize, kr_stream_t stream);
+
 /* ------------------------------------------------------------------------ */
 /* Ragged batch: many independent operations in one persistent launch.      */
 /* ------------------------------------------------------------------------ */

@@ -96,6 +96,7 @@ def load():
         lib.kr_warp_affine.argtypes = [P(KrImage), P(KrImage), P(ctypes.c_float), P(KrPost), ctypes.c_void_p]
         lib.kr_rgb_to_gray.argtypes = [P(KrImage), P(KrImage), ctypes.c_void_p]
         lib.kr_resize_nearest.argtypes = [P(KrImage), P(KrImage), ctypes.c_void_p]
+        lib.kr_sobel.argtypes = [P(KrImage), P(KrImage), ctypes.c_int32, ctypes.c_void_p]
         lib.kr_warp_perspective.argtypes = [P(KrImage), P(KrImage), P(ctypes.c_float), P(KrPost), ctypes.c_void_p]
         lib.kr_flip_horizontal.argtypes = [P(KrImage), P(KrImage), ctypes.c_void_p]
         lib.kr_batch_workspace_size.argtypes = [ctypes.c_int32]
@@ -119,7 +120,7 @@ def load():
         lib.kr_shutdown.argtypes = []
         lib.kr_shutdown.restype = None
         for f in ("kr_resize_bilinear", "kr_warp_affine", "kr_warp_perspective", "kr_rgb_to_gray", "kr_resize_nearest",
-                  "kr_flip_horizontal", "kr_batch_submit",
+                  "kr_flip_horizontal", "kr_sobel", "kr_batch_submit",
                   "kr_batch_submit_noalloc", "kr_serve_run", "kr_device_errors",
                   "kr_tile_config_shape", "kr_autotune_batch", "kr_autotune_save", "kr_autotune_load"):
             getattr(lib, f).restype = S
@@ -251,6 +252,13 @@ def kr_flip_horizontal(src, dst, stream=None):
     lib = load()
     s, d = image(src), image(dst)
     _check(lib.kr_flip_horizontal(ctypes.byref(s), ctypes.byref(d), _stream(stream)), "kr_flip_horizontal")
+
+
+def kr_sobel(src, dst, ksize=3, stream=None):
+    """Sobel 3x3 magnitude of u8 HWC `src` (RGB: of its gray) into single-channel u8 or f32 `dst`."""
+    lib = load()
+    s, d = image(src), image(dst)
+    _check(lib.kr_sobel(ctypes.byref(s), ctypes.byref(d), int(ksize), _stream(stream)), "kr_sobel")
 
 
 def work_item(op, src, dst, M=None, gray=False, mean=None, std=None, dst_layout="hwc") -> KrWork:

@@ -199,6 +199,36 @@ kr_status kr_resize_nearest(const kr_image_t *src, const kr_image_t *dst, kr_str
     return KR_OK;
 }
 
+kr_status kr_sobel(const kr_image_t *src, const kr_image_t *dst, int32_t ksize, kr_stream_t stream)
+{
+    kr_status st;
+    if ((st = check_image(src, false)) != KR_OK) return st;
+    if ((st = check_image(dst, true)) != KR_OK) return st;
+    if (ksize != 3) return KR_ERR_UNSUPPORTED;
+    if (src->dtype != KR_U8 || src->layout != KR_HWC || dst->layout != KR_HWC) return KR_ERR_UNSUPPORTED;
+    if (dst->channels != 1 || src->height != dst->height || src->width != dst->width || src->batch != dst->batch)
+        return KR_ERR_INVALID_ARG;
+    if ((st = check_alias(*src, *dst)) != KR_OK) return st;
+    SobelDesc d;
+    d.src = (const uint8_t *)src->data;
+    d.spitch = src->pitch;
+    d.sbatch = src->batch > 1 ? src->batch_stride : 0;
+    d.H = src->height;
+    d.W = src->width;
+    d.dst = (uint8_t *)dst->data;
+    d.dpitch = dst->pitch;
+    d.dbatch = dst->batch > 1 ? dst->batch_stride : 0;
+    d.C = src->channels;
+    d.f32 = dst->dtype == KR_F32;
+    d.batch = src->batch;
+    cudaError_t e = launch_sobel(d, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        set_last_error("kr_sobel", e);
+        return KR_ERR_CUDA;
+    }
+    return KR_OK;
+}
+
 kr_status kr_flip_horizontal(const kr_image_t *src, const kr_image_t *dst, kr_stream_t stream)
 {
     GatherDesc d;

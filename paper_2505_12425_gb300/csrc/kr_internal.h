@@ -60,6 +60,19 @@ struct GatherDesc {
     int batch;
 };
 cudaError_t launch_resize_nearest(const GatherDesc &d, cudaStream_t stream);
+
+// Sobel 3x3 magnitude: u8 HWC source (C = 1 or 3), single-channel u8 or f32 HWC output.
+struct SobelDesc {
+    const uint8_t *src;
+    int64_t spitch, sbatch;
+    int H, W;
+    uint8_t *dst;
+    int64_t dpitch, dbatch;
+    int C;
+    int f32;
+    int batch;
+};
+cudaError_t launch_sobel(const SobelDesc &d, cudaStream_t stream);
 cudaError_t launch_flip_h(const GatherDesc &d, cudaStream_t stream);
 
 // Shared-memory budget of one tile: region A bytes (0 = no staging) and region B bytes

@@ -110,6 +110,15 @@ def test_perspective_rejects_bad_maps(lib):
     assert lib.kr_warp_perspective(ctypes.byref(s), ctypes.byref(_img(data=0x10001)), a, ctypes.byref(p), None) == 3
 
 
+def test_sobel_rejects_bad_arguments(lib):
+    s = _img()
+    d = _img(data=0x900000, c=1)
+    assert lib.kr_sobel(ctypes.byref(s), ctypes.byref(d), 5, None) == 2          # only 3 x 3
+    assert lib.kr_sobel(ctypes.byref(s), ctypes.byref(_img(data=0x900000, c=3)), 3, None) == 1
+    assert lib.kr_sobel(ctypes.byref(s), ctypes.byref(_img(data=0x900000, c=1, w=4)), 3, None) == 1
+    assert lib.kr_sobel(ctypes.byref(s), ctypes.byref(_img(data=0x10001, c=1)), 3, None) == 3
+
+
 def test_gathers_reject_bad_shapes(lib):
     s = _img()
     for f in (lib.kr_resize_nearest, lib.kr_flip_horizontal):

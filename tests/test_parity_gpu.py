@@ -476,3 +476,38 @@ def test_perspective_behind_the_camera_is_the_zero_sample():
     torch.cuda.synchronize()
     assert not u.np().any()
     np.testing.assert_allclose(f.np(), np.broadcast_to(-np.array(MEAN) / np.array(STD), (H, W, 3)), atol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Sobel 3x3
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("H,W,C", [(1080, 1920, 3), (1, 1, 3), (2, 3, 1), (7, 13, 3), (33, 65, 1), (100, 129, 3)])
+def test_sobel(H, W, C):
+    img = inputs.noise_gradient_image(H + W, H, W, C) if C == 3 else inputs.uniform_image(H + W, H, W, 1)
+    f = Guarded((H, W, 1), torch.float32)
+    u = Guarded((H, W, 1), torch.uint8)
+    kr.kr_sobel(to_dev(img), f.t)
+    kr.kr_sobel(to_dev(img), u.t)
+    torch.cuda.synchronize()
+    f.check()
+    u.check()
+    rf, ru = oracle.sobel(img)
+    np.testing.assert_array_equal(f.np(), rf)          # the same fp32 operations: bit for bit
+    np.testing.assert_array_equal(u.np(), ru)
+
+
+def test_sobel_on_views_and_batches():
+    n, H, W = 3, 45, 70
+    imgs = np.stack([inputs.noise_gradient_image(90 + i, H, W) for i in range(n)])
+    big = torch.full((n, H + 3, W + 4, 3), 250, dtype=torch.uint8, device=dev())
+    big[:, 1:1 + H, 2:2 + W] = to_dev(imgs)
+    src = big[:, 1:1 + H, 2:2 + W]
+    dbig = torch.full((n, H + 2, W + 6, 1), -3.0, dtype=torch.float32, device=dev())
+    dst = dbig[:, 1:1 + H, 3:3 + W]
+    kr.kr_sobel(src, dst)
+    torch.cuda.synchronize()
+    m = torch.ones(dbig.shape[:3], dtype=torch.bool, device=dev())
+    m[:, 1:1 + H, 3:3 + W] = False
+    assert bool((dbig[m] == -3.0).all()), "write outside the destination view"
+    for i in range(n):
+        np.testing.assert_array_equal(dst[i].cpu().numpy(), oracle.sobel(imgs[i])[0])
