@@ -66,6 +66,10 @@ def _load():
             lib.oracle_warp_persp_f64.argtypes = [_u8p, _L, _L, _L, _f32p, _f64p, _L, _L, ctypes.c_int,
                                                   _f64p, _f64p, _u8p]
             lib.oracle_persp_point.argtypes = [_f32p, _L, _L, _f32p, _f32p, _lp, _lp, _lp, _lp]
+            lib.oracle_warp_ex_u8.argtypes = [_u8p, _L, _L, _L, _f32p, ctypes.c_int, ctypes.c_int, _u8p, _L, _L,
+                                              ctypes.c_int, _u8p]
+            lib.oracle_warp_ex_f64.argtypes = [_u8p, _L, _L, _L, _f32p, ctypes.c_int, ctypes.c_int, _f64p, _L,
+                                               _L, ctypes.c_int, _f64p, _f64p, _u8p]
             lib.oracle_flip_h_u8.argtypes = [_u8p, _L, _L, _L, _u8p]
             lib.oracle_sobel.argtypes = [_u8p, _L, _L, _L, _f32p, _u8p]
             for f in (lib.oracle_resize_u8, lib.oracle_resize_f64, lib.oracle_warp_u8,
@@ -132,8 +136,40 @@ def _mat(M, n=6):
     return M
 
 
-def warp_u8(img, M, h, w, gray=False, touched=False):
-    """Affine warp (M: 2x3 destination->source, fp32), zero border, u8 fixed point."""
+_BORDERS = {"zero": 0, "replicate": 1}
+
+
+def _warp_ex_u8(img, M, h, w, persp, border, gray, touched):
+    src = _src(img)
+    H, W, C = src.shape
+    Mf = _mat(M, 9 if persp else 6)
+    out = np.zeros((h, w, 1 if gray else C), dtype=np.uint8)
+    t = _touched(H, W, touched)
+    rc = _load().oracle_warp_ex_u8(_p(src, _u8p), H, W, C, _p(Mf, _f32p), int(persp), _BORDERS[border],
+                                   _p(out, _u8p), h, w, int(gray), _p(t, _u8p))
+    if rc != 0:
+        raise ValueError("oracle_warp_ex_u8: bad arguments")
+    return (out, t) if touched else out
+
+
+def _warp_ex_f64(img, M, h, w, persp, border, gray, mean, std, touched):
+    src = _src(img)
+    H, W, C = src.shape
+    Mf = _mat(M, 9 if persp else 6)
+    m, s = _norm(C, mean, std)
+    out = np.zeros((h, w, 1 if gray else C), dtype=np.float64)
+    t = _touched(H, W, touched)
+    rc = _load().oracle_warp_ex_f64(_p(src, _u8p), H, W, C, _p(Mf, _f32p), int(persp), _BORDERS[border],
+                                    _p(out, _f64p), h, w, int(gray), _p(m, _f64p), _p(s, _f64p), _p(t, _u8p))
+    if rc != 0:
+        raise ValueError("oracle_warp_ex_f64: bad arguments")
+    return (out, t) if touched else out
+
+
+def warp_u8(img, M, h, w, gray=False, touched=False, border="zero"):
+    """Affine warp (M: 2x3 destination->source, fp32), zero or replicated border, u8 fixed point."""
+    if border != "zero":
+        return _warp_ex_u8(img, M, h, w, False, border, gray, touched)
     src = _src(img)
     H, W, C = src.shape
     Mf = _mat(M)
@@ -146,8 +182,10 @@ def warp_u8(img, M, h, w, gray=False, touched=False):
     return (out, t) if touched else out
 
 
-def warp_f64(img, M, h, w, gray=False, mean=None, std=None, touched=False):
-    """Affine warp of p/255 in double (fp32 coordinate), zero border, normalised."""
+def warp_f64(img, M, h, w, gray=False, mean=None, std=None, touched=False, border="zero"):
+    """Affine warp of p/255 in double (fp32 coordinate), zero or replicated border, normalised."""
+    if border != "zero":
+        return _warp_ex_f64(img, M, h, w, False, border, gray, mean, std, touched)
     src = _src(img)
     H, W, C = src.shape
     Mf = _mat(M)
@@ -209,8 +247,10 @@ def flip_h_u8(img):
     return out
 
 
-def warp_persp_u8(img, M, h, w, gray=False, touched=False):
-    """Perspective warp (M: 3x3 destination->source, fp32), zero border, u8 fixed point."""
+def warp_persp_u8(img, M, h, w, gray=False, touched=False, border="zero"):
+    """Perspective warp (M: 3x3 destination->source, fp32), zero or replicated border, u8 fixed point."""
+    if border != "zero":
+        return _warp_ex_u8(img, M, h, w, True, border, gray, touched)
     src = _src(img)
     H, W, C = src.shape
     Mf = _mat(M, 9)
@@ -223,8 +263,10 @@ def warp_persp_u8(img, M, h, w, gray=False, touched=False):
     return (out, t) if touched else out
 
 
-def warp_persp_f64(img, M, h, w, gray=False, mean=None, std=None, touched=False):
-    """Perspective warp of p/255 in double (fp32 coordinate), zero border, normalised."""
+def warp_persp_f64(img, M, h, w, gray=False, mean=None, std=None, touched=False, border="zero"):
+    """Perspective warp of p/255 in double (fp32 coordinate), zero or replicated border, normalised."""
+    if border != "zero":
+        return _warp_ex_f64(img, M, h, w, True, border, gray, mean, std, touched)
     src = _src(img)
     H, W, C = src.shape
     Mf = _mat(M, 9)

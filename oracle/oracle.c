@@ -19,6 +19,8 @@
  *   - perspective warp with a 3x3 inverse map (the projective generalisation
  *     of the affine warp; Sec. II-A "geometric transforms"), same taps,
  *     weights and border as the affine warp;
+ *   - a replicate-border variant of both warps (taps outside the image read the
+ *     nearest edge pixel instead of zero);
  *   - Sobel 3x3 gradient magnitude (Sec. V: the robotics example's
  *     imgproc::filter::sobel(&img, &mut out, 3), RGB8 in, Gray8 out).
  *
@@ -244,14 +246,28 @@ static void warp_weight(float s, long *i0, long *q)
     *q = k + ((t - (float)k) >= 0.5f ? 1 : 0);
 }
 
-static long tap_u8(const uint8_t *src, long H, long W, long C, long y, long x, long c)
+/* Border modes of the warps: zero outside the image, or the nearest edge pixel. */
+#define BORDER_ZERO 0
+#define BORDER_REPLICATE 1
+
+static long clamp_index(long v, long n) { return v < 0 ? 0 : (v >= n ? n - 1 : v); }
+
+static long tap_u8(const uint8_t *src, long H, long W, long C, long y, long x, long c, int border)
 {
+    if (border == BORDER_REPLICATE) {
+        x = clamp_index(x, W);
+        y = clamp_index(y, H);
+    }
     if (x < 0 || x >= W || y < 0 || y >= H) return 0;
     return src[(y * W + x) * C + c];
 }
 
-static void mark_in(uint8_t *touched, long H, long W, long y, long x)
+static void mark_in(uint8_t *touched, long H, long W, long y, long x, int border)
 {
+    if (border == BORDER_REPLICATE) {
+        x = clamp_index(x, W);
+        y = clamp_index(y, H);
+    }
     if (x >= 0 && x < W && y >= 0 && y < H) mark(touched, W, y, x);
 }
 
@@ -259,7 +275,7 @@ static void mark_in(uint8_t *touched, long H, long W, long y, long x)
 /* Affine (persp = 0; M: 6 floats, row-major 2x3) or perspective (persp = 1; */
 /* M: 9 floats, row-major 3x3) warp, u8 out (zero border per tap).          */
 /* ======================================================================== */
-static int warp_u8_impl(const uint8_t *src, long H, long W, long C, const float *M, int persp,
+static int warp_u8_impl(const uint8_t *src, long H, long W, long C, const float *M, int persp, int border,
                         uint8_t *dst, long h, long w, int gray, uint8_t *touched)
 {
     if (H < 1 || W < 1 || h < 1 || w < 1 || (C != 1 && C != 3)) return ORACLE_BAD;
@@ -274,16 +290,16 @@ static int warp_u8_impl(const uint8_t *src, long H, long W, long C, const float 
                 warp_weight(sx, &x0, &qx);
                 warp_weight(sy, &y0, &qy);
                 for (long c = 0; c < C; ++c) {
-                    long p00 = tap_u8(src, H, W, C, y0, x0, c);
-                    long p01 = tap_u8(src, H, W, C, y0, x0 + 1, c);
-                    long p10 = tap_u8(src, H, W, C, y0 + 1, x0, c);
-                    long p11 = tap_u8(src, H, W, C, y0 + 1, x0 + 1, c);
+                    long p00 = tap_u8(src, H, W, C, y0, x0, c, border);
+                    long p01 = tap_u8(src, H, W, C, y0, x0 + 1, c, border);
+                    long p10 = tap_u8(src, H, W, C, y0 + 1, x0, c, border);
+                    long p11 = tap_u8(src, H, W, C, y0 + 1, x0 + 1, c, border);
                     out[c] = blend_u8(p00, p01, p10, p11, qx, qy);
                 }
-                if (qx < 2048 && qy < 2048) mark_in(touched, H, W, y0, x0);
-                if (qx > 0 && qy < 2048) mark_in(touched, H, W, y0, x0 + 1);
-                if (qx < 2048 && qy > 0) mark_in(touched, H, W, y0 + 1, x0);
-                if (qx > 0 && qy > 0) mark_in(touched, H, W, y0 + 1, x0 + 1);
+                if (qx < 2048 && qy < 2048) mark_in(touched, H, W, y0, x0, border);
+                if (qx > 0 && qy < 2048) mark_in(touched, H, W, y0, x0 + 1, border);
+                if (qx < 2048 && qy > 0) mark_in(touched, H, W, y0 + 1, x0, border);
+                if (qx > 0 && qy > 0) mark_in(touched, H, W, y0 + 1, x0 + 1, border);
             }
             if (gray) {
                 dst[y * w + x] = (uint8_t)gray_u8(out[0], out[1], out[2]);
@@ -298,17 +314,21 @@ static int warp_u8_impl(const uint8_t *src, long H, long W, long C, const float 
 int oracle_warp_u8(const uint8_t *src, long H, long W, long C, const float *M,
                    uint8_t *dst, long h, long w, int gray, uint8_t *touched)
 {
-    return warp_u8_impl(src, H, W, C, M, 0, dst, h, w, gray, touched);
+    return warp_u8_impl(src, H, W, C, M, 0, BORDER_ZERO, dst, h, w, gray, touched);
 }
 
 int oracle_warp_persp_u8(const uint8_t *src, long H, long W, long C, const float *M,
                          uint8_t *dst, long h, long w, int gray, uint8_t *touched)
 {
-    return warp_u8_impl(src, H, W, C, M, 1, dst, h, w, gray, touched);
+    return warp_u8_impl(src, H, W, C, M, 1, BORDER_ZERO, dst, h, w, gray, touched);
 }
 
-static double tap_f64(const uint8_t *src, long H, long W, long C, long y, long x, long c)
+static double tap_f64(const uint8_t *src, long H, long W, long C, long y, long x, long c, int border)
 {
+    if (border == BORDER_REPLICATE) {
+        x = clamp_index(x, W);
+        y = clamp_index(y, H);
+    }
     if (x < 0 || x >= W || y < 0 || y >= H) return 0.0;
     return src[(y * W + x) * C + c] / 255.0;
 }
@@ -318,7 +338,7 @@ static double tap_f64(const uint8_t *src, long H, long W, long C, long y, long x
 /* fp32 value from warp_coord / persp_coord; the fraction s - floor(s) is    */
 /* taken exactly in double and not quantised.                               */
 /* ======================================================================== */
-static int warp_f64_impl(const uint8_t *src, long H, long W, long C, const float *M, int persp,
+static int warp_f64_impl(const uint8_t *src, long H, long W, long C, const float *M, int persp, int border,
                          double *dst, long h, long w, int gray,
                          const double *mean, const double *stdv, uint8_t *touched)
 {
@@ -335,17 +355,17 @@ static int warp_f64_impl(const uint8_t *src, long H, long W, long C, const float
                 double fx = dsx - fx0, fy = dsy - fy0;
                 long x0 = (long)fx0, y0 = (long)fy0;
                 for (long c = 0; c < C; ++c) {
-                    double a = tap_f64(src, H, W, C, y0, x0, c);
-                    double b = tap_f64(src, H, W, C, y0, x0 + 1, c);
-                    double d0 = tap_f64(src, H, W, C, y0 + 1, x0, c);
-                    double d1 = tap_f64(src, H, W, C, y0 + 1, x0 + 1, c);
+                    double a = tap_f64(src, H, W, C, y0, x0, c, border);
+                    double b = tap_f64(src, H, W, C, y0, x0 + 1, c, border);
+                    double d0 = tap_f64(src, H, W, C, y0 + 1, x0, c, border);
+                    double d1 = tap_f64(src, H, W, C, y0 + 1, x0 + 1, c, border);
                     v[c] = (1.0 - fy) * ((1.0 - fx) * a + fx * b)
                          + fy * ((1.0 - fx) * d0 + fx * d1);
                 }
-                if (fx < 1.0 && fy < 1.0) mark_in(touched, H, W, y0, x0);
-                if (fx > 0.0 && fy < 1.0) mark_in(touched, H, W, y0, x0 + 1);
-                if (fx < 1.0 && fy > 0.0) mark_in(touched, H, W, y0 + 1, x0);
-                if (fx > 0.0 && fy > 0.0) mark_in(touched, H, W, y0 + 1, x0 + 1);
+                if (fx < 1.0 && fy < 1.0) mark_in(touched, H, W, y0, x0, border);
+                if (fx > 0.0 && fy < 1.0) mark_in(touched, H, W, y0, x0 + 1, border);
+                if (fx < 1.0 && fy > 0.0) mark_in(touched, H, W, y0 + 1, x0, border);
+                if (fx > 0.0 && fy > 0.0) mark_in(touched, H, W, y0 + 1, x0 + 1, border);
             }
             if (gray) {
                 dst[y * w + x] = (gray_f64(v[0], v[1], v[2]) - mean[0]) / stdv[0];
@@ -362,14 +382,30 @@ int oracle_warp_f64(const uint8_t *src, long H, long W, long C, const float *M,
                     double *dst, long h, long w, int gray,
                     const double *mean, const double *stdv, uint8_t *touched)
 {
-    return warp_f64_impl(src, H, W, C, M, 0, dst, h, w, gray, mean, stdv, touched);
+    return warp_f64_impl(src, H, W, C, M, 0, BORDER_ZERO, dst, h, w, gray, mean, stdv, touched);
 }
 
 int oracle_warp_persp_f64(const uint8_t *src, long H, long W, long C, const float *M,
                           double *dst, long h, long w, int gray,
                           const double *mean, const double *stdv, uint8_t *touched)
 {
-    return warp_f64_impl(src, H, W, C, M, 1, dst, h, w, gray, mean, stdv, touched);
+    return warp_f64_impl(src, H, W, C, M, 1, BORDER_ZERO, dst, h, w, gray, mean, stdv, touched);
+}
+
+/* Either warp (persp = 0: M 2x3, 1: M 3x3) with either border (0 zero, 1 replicate). */
+int oracle_warp_ex_u8(const uint8_t *src, long H, long W, long C, const float *M, int persp, int border,
+                      uint8_t *dst, long h, long w, int gray, uint8_t *touched)
+{
+    if (border != BORDER_ZERO && border != BORDER_REPLICATE) return ORACLE_BAD;
+    return warp_u8_impl(src, H, W, C, M, persp != 0, border, dst, h, w, gray, touched);
+}
+
+int oracle_warp_ex_f64(const uint8_t *src, long H, long W, long C, const float *M, int persp, int border,
+                       double *dst, long h, long w, int gray,
+                       const double *mean, const double *stdv, uint8_t *touched)
+{
+    if (border != BORDER_ZERO && border != BORDER_REPLICATE) return ORACLE_BAD;
+    return warp_f64_impl(src, H, W, C, M, persp != 0, border, dst, h, w, gray, mean, stdv, touched);
 }
 
 /* ======================================================================== */

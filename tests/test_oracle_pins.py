@@ -536,3 +536,51 @@ def test_sobel_commutes_with_transpose_and_fuses_gray():
     np.testing.assert_array_equal(f, fg)
     ft, _ = oracle.sobel(np.ascontiguousarray(g.transpose(1, 0, 2)))
     np.testing.assert_array_equal(ft, f.transpose(1, 0, 2))
+
+
+# ---------------------------------------------------------------------------
+# Replicate border (both warps)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("dx,dy", [(3, -2), (-5, 4), (0, 7), (40, -30)])
+def test_replicate_integer_shift_is_the_edge_padded_window(dx, dy):
+    H, W = 21, 27
+    img = inputs.uniform_image(140, H, W, 3)
+    M = np.array([[1, 0, dx], [0, 1, dy]], np.float32)        # out(x, y) = in(x + dx, y + dy)
+    ys = np.clip(np.arange(H) + dy, 0, H - 1)
+    xs = np.clip(np.arange(W) + dx, 0, W - 1)
+    ref = img[np.ix_(ys, xs)]
+    np.testing.assert_array_equal(oracle.warp_u8(img, M, H, W, border="replicate"), ref)
+    P = np.vstack([M, [0, 0, 1]]).astype(np.float32)
+    np.testing.assert_array_equal(oracle.warp_persp_u8(img, P, H, W, border="replicate"), ref)
+
+
+def test_replicate_matches_torch_grid_sample_border_mode():
+    H, W = 17, 23
+    img = inputs.uniform_image(141, H, W, 3)
+    M = inputs.random_inverse_affine(np.random.default_rng(142), H, W, k=1.3)
+    got = oracle.warp_f64(img, M, H, W, border="replicate")
+    gx, gy = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    Md = M.astype(np.float64)
+    sx = Md[0, 0] * gx + Md[0, 1] * gy + Md[0, 2]              # continuous source position
+    sy = Md[1, 0] * gx + Md[1, 1] * gy + Md[1, 2]
+    grid = torch.from_numpy(np.stack([2 * sx / W - 1, 2 * sy / H - 1], -1)[None])
+    t = torch.from_numpy(img.transpose(2, 0, 1)[None].astype(np.float64) / 255.0)
+    ref = F.grid_sample(t, grid, mode="bilinear", padding_mode="border", align_corners=False)[0]
+    ref = ref.numpy().transpose(1, 2, 0)
+    assert np.abs(got - ref).max() < 1e-5                        # fp32 vs fp64 coordinates
+
+
+def test_replicate_equals_zero_border_inside_and_fills_outside():
+    H, W = 30, 40
+    img = inputs.noise_gradient_image(143, H, W)
+    M = inputs.random_inverse_affine(np.random.default_rng(144), H, W)
+    z = oracle.warp_u8(img, M, H, W)
+    r = oracle.warp_u8(img, M, H, W, border="replicate")
+    inside = np.zeros((H, W), bool)
+    for y in range(H):
+        for x in range(W):
+            ok, sx, sy, *_ = oracle.warp_point(M, x, y)
+            inside[y, x] = ok and 0 <= sx <= W - 1 and 0 <= sy <= H - 1 and math.floor(sx) + 1 < W \
+                and math.floor(sy) + 1 < H
+    np.testing.assert_array_equal(r[inside], z[inside])
+    assert r[~inside].any() and (r[~inside] != z[~inside]).any()
