@@ -98,6 +98,8 @@ typedef struct {
 /* Fused epilogue flags. */
 #define KR_GRAY      1u   /* 3-channel source -> 1-channel destination (BT.601)          */
 #define KR_NORMALIZE 2u   /* f32 destination: (v - mean[c]) / std[c]; needs dtype KR_F32 */
+#define KR_BORDER_REPLICATE 4u /* warps only: taps outside the image read the nearest edge
+                                  pixel instead of zero (resize: KR_ERR_INVALID_ARG) */
 
 /*
  * Fused epilogue (Sec. III: RGB to grayscale; u8 -> f32 normalisation).

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "libkr.so")
 
 KR_U8, KR_F32 = 0, 1
 KR_HWC, KR_CHW = 0, 1
-KR_GRAY, KR_NORMALIZE = 1, 2
+KR_GRAY, KR_NORMALIZE, KR_BORDER_REPLICATE = 1, 2, 4
 KR_OP_RESIZE, KR_OP_WARP, KR_OP_GRAY = 0, 1, 2
 
 STATUS = {0: "KR_OK", 1: "KR_ERR_INVALID_ARG", 2: "KR_ERR_UNSUPPORTED", 3: "KR_ERR_ALIAS",
@@ -186,9 +186,12 @@ def image(t: torch.Tensor, layout: str = "hwc") -> KrImage:
     return im
 
 
-def post(gray: bool = False, mean=None, std=None) -> KrPost:
+def post(gray: bool = False, mean=None, std=None, border: str = "zero") -> KrPost:
+    if border not in ("zero", "replicate"):
+        raise ValueError(f"border must be 'zero' or 'replicate', got {border!r}")
     p = KrPost()
-    p.flags = (KR_GRAY if gray else 0) | (KR_NORMALIZE if (mean is not None or std is not None) else 0)
+    p.flags = (KR_GRAY if gray else 0) | (KR_NORMALIZE if (mean is not None or std is not None) else 0) | \
+        (KR_BORDER_REPLICATE if border == "replicate" else 0)
     m = (0.0, 0.0, 0.0) if mean is None else tuple(float(v) for v in mean)
     s = (1.0, 1.0, 1.0) if std is None else tuple(float(v) for v in std)
     for i in range(3):
@@ -213,20 +216,21 @@ def _mats(M, n, k=6):
     return a
 
 
-def kr_warp_affine(src, dst, M, gray=False, mean=None, std=None, dst_layout="hwc", stream=None):
+def kr_warp_affine(src, dst, M, gray=False, mean=None, std=None, dst_layout="hwc", stream=None, border="zero"):
     """Affine warp (M: (N,) 2x3 destination->source maps) of u8 HWC `src` into `dst`."""
     lib = load()
-    s, d, p = image(src), image(dst, dst_layout), post(gray, mean, std)
+    s, d, p = image(src), image(dst, dst_layout), post(gray, mean, std, border)
     a = _mats(M, s.batch)
     _check(lib.kr_warp_affine(ctypes.byref(s), ctypes.byref(d),
                               a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(p),
                               _stream(stream)), "kr_warp_affine")
 
 
-def kr_warp_perspective(src, dst, M, gray=False, mean=None, std=None, dst_layout="hwc", stream=None):
+def kr_warp_perspective(src, dst, M, gray=False, mean=None, std=None, dst_layout="hwc", stream=None,
+                        border="zero"):
     """Perspective warp (M: (N,) 3x3 destination->source maps) of u8 HWC `src` into `dst`."""
     lib = load()
-    s, d, p = image(src), image(dst, dst_layout), post(gray, mean, std)
+    s, d, p = image(src), image(dst, dst_layout), post(gray, mean, std, border)
     a = _mats(M, s.batch, 9)
     _check(lib.kr_warp_perspective(ctypes.byref(s), ctypes.byref(d),
                                    a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(p),
@@ -261,7 +265,7 @@ def kr_sobel(src, dst, ksize=3, stream=None):
     _check(lib.kr_sobel(ctypes.byref(s), ctypes.byref(d), int(ksize), _stream(stream)), "kr_sobel")
 
 
-def work_item(op, src, dst, M=None, gray=False, mean=None, std=None, dst_layout="hwc") -> KrWork:
+def work_item(op, src, dst, M=None, gray=False, mean=None, std=None, dst_layout="hwc", border="zero") -> KrWork:
     """One kr_work_t (batch == 1 images)."""
     w = KrWork()
     w.op = op
@@ -271,7 +275,7 @@ def work_item(op, src, dst, M=None, gray=False, mean=None, std=None, dst_layout=
         a = _mats(M, 1)
         for i in range(6):
             w.M[i] = float(a[i])
-    w.post = post(gray, mean, std)
+    w.post = post(gray, mean, std, border)
     return w
 
 

@@ -90,7 +90,8 @@ kr_status build_resample(int op, const kr_image_t *src, const kr_image_t *dst, c
     if (src->dtype != KR_U8) return KR_ERR_UNSUPPORTED;
     if (src->batch != dst->batch) return KR_ERR_INVALID_ARG;
     const uint32_t flags = post ? post->flags : 0u;
-    if (flags & ~(KR_GRAY | KR_NORMALIZE)) return KR_ERR_INVALID_ARG;
+    if (flags & ~(KR_GRAY | KR_NORMALIZE | KR_BORDER_REPLICATE)) return KR_ERR_INVALID_ARG;
+    if ((flags & KR_BORDER_REPLICATE) && op == OP_RESIZE) return KR_ERR_INVALID_ARG;
     const bool gray = flags & KR_GRAY, norm = flags & KR_NORMALIZE;
     if (gray) {
         if (src->channels != 3 || dst->channels != 1) return KR_ERR_INVALID_ARG;
@@ -117,6 +118,7 @@ kr_status build_resample(int op, const kr_image_t *src, const kr_image_t *dst, c
     d.h = dst->height;
     d.w = dst->width;
     d.chw = dst->layout == KR_CHW && dst->channels == 3;
+    d.replicate = (flags & KR_BORDER_REPLICATE) ? 1 : 0;
     d.batch = src->batch;
     for (int c = 0; c < 3; ++c) {
         double mean = 0.0, stdv = 1.0;

@@ -78,8 +78,8 @@ struct alignas(16) WsHeader {
 };
 static_assert(sizeof(WsHeader) == 512, "header is 512 bytes");
 // item flags: the warp map allows the fast path; region A is sized for raw boxes; the
-// source rows are 16-byte aligned (bulk row copies)
-constexpr int ITEM_FAST = 1, ITEM_RAW = 2, ITEM_ROWS16 = 4;
+// source rows are 16-byte aligned (bulk row copies); the warp replicates the border
+constexpr int ITEM_FAST = 1, ITEM_RAW = 2, ITEM_ROWS16 = 4, ITEM_REPLICATE = 8;
 
 // Device error flags of the ragged kernel (bit 0: a bounded staging wait ran out).
 static __device__ unsigned g_kr_batch_err;
@@ -123,6 +123,7 @@ __device__ __forceinline__ Job job_of(const WorkItem &it)
     J.tin_nc = J.tin_br = 0;
     J.raw_taps = (it.flags & ITEM_RAW) ? 1 : 0;
     J.rows16 = (it.flags & ITEM_ROWS16) ? 1 : 0;
+    J.replicate = (it.flags & ITEM_REPLICATE) ? 1 : 0;
     J.tout = nullptr;
     J.zimg = 0;
     J.err = &g_kr_batch_err;
@@ -279,6 +280,7 @@ static kr_status build_item(const kr_work_t &w, int tw, int th, int smem_cap, Wo
         it.flags = (op == OP_RESIZE || warp_allows_fast(it.M, d.h, d.w)) ? ITEM_FAST : 0;
         const bool rows16 = ((uintptr_t)d.src & 15) == 0 && (d.spitch & 15) == 0;
         if (rows16) it.flags |= ITEM_ROWS16;
+        if (d.replicate) it.flags |= ITEM_REPLICATE;
         if (d.cin == 3 && rows16 && bud.a > 0 && bud.fits) {
             // bulk row copies and raw taps: region A holds the item's largest box (plus
             // the 16 bytes a last pixel pair may touch), region B only the output tile

@@ -57,6 +57,7 @@ struct Job {
     int32_t raw_taps;     // region A is sized for raw boxes: 3-channel tiles staged by TMA or by
                           // bulk row copies read their taps from the raw rows, not re-laid words
     int32_t rows16;       // source base and pitch are 16-byte aligned (bulk row copies possible)
+    int32_t replicate;    // warps: taps outside the image read the nearest edge pixel (else zero)
     // TMA (per-operation kernels; null in the ragged kernel). Both maps view images as
     // {32-bit word, row, (plane,) image} tensors whose rows are a whole number of words.
     const CUtensorMap *tin;   // source map, box {4 tin_nc words, tin_br rows, 1}; null = cp.async staging
@@ -311,18 +312,27 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 // Bound of every TMA wait: far above any copy's latency, far below a hang.
 constexpr uint64_t kTmaWaitNs = 2000000000ull;
 
-// One RGB pixel from global memory as a word R | G << 8 | B << 16 (zero outside the image).
+// One RGB pixel from global memory as a word R | G << 8 | B << 16 (outside the image: zero,
+// or with `rep` the nearest edge pixel).
 __device__ __forceinline__ uint32_t ldg_px3(const uint8_t *src, int64_t spitch, int H, int W, int y,
-                                            int x)
+                                            int x, bool rep = false)
 {
+    if (rep) {
+        x = min(max(x, 0), W - 1);
+        y = min(max(y, 0), H - 1);
+    }
     if ((unsigned)x >= (unsigned)W || (unsigned)y >= (unsigned)H) return 0u;
     const uint8_t *p = src + (int64_t)y * spitch + (int64_t)x * 3;
     return (uint32_t)__ldg(p) | ((uint32_t)__ldg(p + 1) << 8) | ((uint32_t)__ldg(p + 2) << 16);
 }
 
 __device__ __forceinline__ uint32_t ldg_px1(const uint8_t *src, int64_t spitch, int H, int W, int y,
-                                            int x)
+                                            int x, bool rep = false)
 {
+    if (rep) {
+        x = min(max(x, 0), W - 1);
+        y = min(max(y, 0), H - 1);
+    }
     if ((unsigned)x >= (unsigned)W || (unsigned)y >= (unsigned)H) return 0u;
     return (uint32_t)__ldg(src + (int64_t)y * spitch + x);
 }
@@ -672,7 +682,8 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             if (all_ok) {
                 fx0 = (int)floorf(mnx) - 1; fx1 = (int)floorf(mxx) + 3;
                 fy0 = (int)floorf(mny) - 1; fy1 = (int)floorf(mxy) + 3;
-                zero = fx1 < 0 || fx0 > J.W - 1 || fy1 < 0 || fy0 > J.H - 1;
+                // (with the replicated border no tile is all zero)
+                zero = !J.replicate && (fx1 < 0 || fx0 > J.W - 1 || fy1 < 0 || fy0 > J.H - 1);
                 // the one-fma weight form needs every coordinate in [0, 4094)
                 fast = J.allow_fast && mnx >= 1.f && mny >= 1.f && mxx < 4093.f && mxy < 4093.f;
             }
@@ -688,6 +699,9 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     const int srow = raw_row_bytes(max(cols, 1), CIN), sw = word_row(max(cols, 1));
     const bool zero_tile = OP != OP_RESIZE && ti.zero != 0;
     bool staged = !zero_tile && cols >= 1 && rows >= 1 && J.foot_budget > 0;
+    // The staged box holds zeros outside the image: with the replicated border only boxes
+    // inside the image are staged, the others take the general path.
+    if (OP != OP_RESIZE && J.replicate && (fx0 < 0 || fy0 < 0 || fx1 > J.W - 1 || fy1 > J.H - 1)) staged = false;
     const int bph = (fx0 * CIN) & 15;   // 16-byte phase of the box in every row of 16-byte aligned rows
     const bool mbar_ok = FRESH || ts.mbar_ok != 0;
     // (1) one TMA copy when the launch has a source map whose box holds this tile's box
@@ -1126,15 +1140,17 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                             const uint8_t *s1 = raw + r1 * rstride + ph1 + (x0 - fx0);
                             p00 = s0[0]; p01 = s0[dx]; p10 = s1[0]; p11 = s1[dx];
                         } else if (CIN == 3) {
-                            p00 = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0);
-                            p01 = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0 + dx);
-                            p10 = ldg_px3(J.src, J.spitch, J.H, J.W, y0 + dy, x0);
-                            p11 = ldg_px3(J.src, J.spitch, J.H, J.W, y0 + dy, x0 + dx);
+                            const bool rp = OP != OP_RESIZE && J.replicate;
+                            p00 = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0, rp);
+                            p01 = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0 + dx, rp);
+                            p10 = ldg_px3(J.src, J.spitch, J.H, J.W, y0 + dy, x0, rp);
+                            p11 = ldg_px3(J.src, J.spitch, J.H, J.W, y0 + dy, x0 + dx, rp);
                         } else {
-                            p00 = ldg_px1(J.src, J.spitch, J.H, J.W, y0, x0);
-                            p01 = ldg_px1(J.src, J.spitch, J.H, J.W, y0, x0 + dx);
-                            p10 = ldg_px1(J.src, J.spitch, J.H, J.W, y0 + dy, x0);
-                            p11 = ldg_px1(J.src, J.spitch, J.H, J.W, y0 + dy, x0 + dx);
+                            const bool rp = OP != OP_RESIZE && J.replicate;
+                            p00 = ldg_px1(J.src, J.spitch, J.H, J.W, y0, x0, rp);
+                            p01 = ldg_px1(J.src, J.spitch, J.H, J.W, y0, x0 + dx, rp);
+                            p10 = ldg_px1(J.src, J.spitch, J.H, J.W, y0 + dy, x0, rp);
+                            p11 = ldg_px1(J.src, J.spitch, J.H, J.W, y0 + dy, x0 + dx, rp);
                         }
                     }
                     emit<CIN, OUTK>(J, o, c, p00, p01, p10, p11, qx, qy, fx, fy);

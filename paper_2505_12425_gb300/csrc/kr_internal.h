@@ -33,6 +33,7 @@ struct OpDesc {
     int batch;
     float scale[3], bias[3];
     const float *M;  // host, 6 * batch floats (warp) or 9 * batch (perspective)
+    int replicate;   // warps: replicated border (else zero)
 };
 
 // Per-op launch (per-image tiles, blockIdx.z = image). Returns cudaSuccess or the launch error.

@@ -39,6 +39,7 @@ struct OpParams {
     int32_t region_b;
     int32_t raw_taps;
     int32_t rows16;
+    int32_t replicate;
     uint32_t fast_mask[(kMaxMPerLaunch + 31) / 32];   // warp: images whose map allows the fast path
     float scale[3], bias[3];
     float M[kMaxMPerLaunch][9];   // warp: 6 floats per image; perspective: 9
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constan
     J.region_b = p.region_b;
     J.raw_taps = p.raw_taps;
     J.rows16 = p.rows16;
+    J.replicate = p.replicate;
     J.allow_fast = OP != OP_RESIZE ? (int)((p.fast_mask[z >> 5] >> (z & 31)) & 1u) : 1;
     J.tin = p.has_tin ? &p.tin : nullptr;
     J.tin_nc = p.tin_nc;
@@ -274,6 +276,7 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
     p.h = d.h;
     p.w = d.w;
     p.chw = d.chw;
+    p.replicate = d.replicate;
     for (int k = 0; k < 3; ++k) {
         p.scale[k] = d.scale[k];
         p.bias[k] = d.bias[k];

@@ -51,6 +51,8 @@ def main():
         add("rgb_to_gray", np.ones((H, W), np.uint8))
         _, p8 = oracle.warp_persp_u8(imgs[i], Ps[i], H, W, touched=True)
         add("warp_persp_u8", p8)
+        _, r8 = oracle.warp_u8(imgs[i], Ms[i], H, W, touched=True, border="replicate")
+        add("warp_u8_replicate", r8)
     out = {
         "workload": f"{n} x {W}x{H}x3 u8 noise+gradient frames (inputs.bench_images / bench_matrices / bench_homographies)",
         "images": n,

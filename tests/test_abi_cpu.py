@@ -98,6 +98,14 @@ def test_warp_rejects_nonfinite_matrix(lib):
     assert lib.kr_warp_affine(ctypes.byref(s), ctypes.byref(d), None, ctypes.byref(p), None) == 1
 
 
+def test_replicate_border_is_for_warps_only(lib):
+    s, d = _img(), _img(data=0x900000)
+    p = kr.post(border="replicate")
+    assert _resize(lib, s, d, p) == 1
+    with pytest.raises(ValueError):
+        kr.post(border="reflect")
+
+
 def test_perspective_rejects_bad_maps(lib):
     s, d, p = _img(), _img(data=0x900000), kr.KrPost()
     assert lib.kr_warp_perspective(ctypes.byref(s), ctypes.byref(d), None, ctypes.byref(p), None) == 1

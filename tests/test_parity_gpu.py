@@ -511,3 +511,52 @@ def test_sobel_on_views_and_batches():
     assert bool((dbig[m] == -3.0).all()), "write outside the destination view"
     for i in range(n):
         np.testing.assert_array_equal(dst[i].cpu().numpy(), oracle.sobel(imgs[i])[0])
+
+
+# ---------------------------------------------------------------------------
+# Replicated border (affine and perspective warps, single images and ragged batches)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("H,W,C,seed", [(1080, 1920, 3, 50), (99, 160, 3, 51), (71, 90, 1, 52)])
+def test_warp_replicate_border(H, W, C, seed):
+    img = inputs.noise_gradient_image(seed, H, W, C)
+    rng = np.random.default_rng(seed)
+    A = inputs.random_inverse_affine(rng, H, W, k=1.4)
+    P = inputs.random_inverse_homography(rng, H, W, tilt=0.6)
+    a = Guarded((H, W, C), torch.uint8)
+    p = Guarded((H, W, C), torch.uint8)
+    kr.kr_warp_affine(to_dev(img), a.t, A, border="replicate")
+    kr.kr_warp_perspective(to_dev(img), p.t, P, border="replicate")
+    torch.cuda.synchronize()
+    a.check()
+    p.check()
+    np.testing.assert_array_equal(a.np(), oracle.warp_u8(img, A, H, W, border="replicate"))
+    np.testing.assert_array_equal(p.np(), oracle.warp_persp_u8(img, P, H, W, border="replicate"))
+    if C == 3:
+        f = Guarded((3, H, W), torch.float32)
+        kr.kr_warp_affine(to_dev(img), f.t, A, mean=MEAN, std=STD, dst_layout="chw", border="replicate")
+        torch.cuda.synchronize()
+        f.check()
+        ref = oracle.warp_f64(img, A, H, W, mean=MEAN, std=STD, border="replicate")
+        assert np.abs(f.np().transpose(1, 2, 0) - ref).max() <= F32_TOL
+
+
+def test_ragged_batch_with_replicate_border():
+    items = []
+    rng = np.random.default_rng(53)
+    srcs, dsts, work = [], [], []
+    for i in range(12):
+        H, W = (int(v) for v in rng.integers(20, 300, 2))
+        img = inputs.uniform_image(530 + i, H, W, 3)
+        M = inputs.random_inverse_affine(rng, H, W, k=1.5)
+        s = to_dev(img)
+        d = torch.empty((H, W, 3), dtype=torch.uint8, device=dev())
+        srcs.append(s)
+        dsts.append(d)
+        items.append((img, M, H, W))
+        work.append(kr.work_item(kr.KR_OP_WARP, s, d, M=M, border="replicate" if i % 2 else "zero"))
+    ws = torch.empty(kr.kr_batch_workspace_size(len(work)), dtype=torch.uint8, device=dev())
+    kr.kr_batch_submit(kr.work_array(work), ws)
+    torch.cuda.synchronize()
+    for i, ((img, M, H, W), d) in enumerate(zip(items, dsts)):
+        ref = oracle.warp_u8(img, M, H, W, border="replicate" if i % 2 else "zero")
+        np.testing.assert_array_equal(d.cpu().numpy(), ref)
