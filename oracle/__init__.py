@@ -72,6 +72,8 @@ def _load():
                                                _L, ctypes.c_int, _f64p, _f64p, _u8p]
             lib.oracle_flip_h_u8.argtypes = [_u8p, _L, _L, _L, _u8p]
             lib.oracle_sobel.argtypes = [_u8p, _L, _L, _L, _f32p, _u8p]
+            lib.oracle_resize_area_u8.argtypes = [_u8p, _L, _L, _L, _u8p, _L, _L]
+            lib.oracle_resize_area_f64.argtypes = [_u8p, _L, _L, _L, _f64p, _L, _L, _f64p, _f64p]
             for f in (lib.oracle_resize_u8, lib.oracle_resize_f64, lib.oracle_warp_u8,
                       lib.oracle_warp_f64, lib.oracle_rgb_to_gray_u8, lib.oracle_warp_point,
                       lib.oracle_resize_point):
@@ -220,6 +222,29 @@ def resize_nearest_u8(img, h, w):
     rc = _load().oracle_resize_nearest_u8(_p(src, _u8p), H, W, C, _p(out, _u8p), h, w)
     if rc != 0:
         raise ValueError("oracle_resize_nearest_u8: bad arguments")
+    return out
+
+
+def resize_area_u8(img, h, w):
+    """Area (overlap-weighted mean) downscale of an H x W x C u8 image to h x w (h <= H, w <= W)."""
+    src = _src(img)
+    H, W, C = src.shape
+    out = np.zeros((h, w, C), dtype=np.uint8)
+    rc = _load().oracle_resize_area_u8(_p(src, _u8p), H, W, C, _p(out, _u8p), h, w)
+    if rc != 0:
+        raise ValueError("oracle_resize_area_u8: bad arguments")
+    return out
+
+
+def resize_area_f64(img, h, w, mean=None, std=None):
+    """Area downscale of p/255 in double, normalised."""
+    src = _src(img)
+    H, W, C = src.shape
+    m, s = _norm(C, mean, std)
+    out = np.zeros((h, w, C), dtype=np.float64)
+    rc = _load().oracle_resize_area_f64(_p(src, _u8p), H, W, C, _p(out, _f64p), h, w, _p(m, _f64p), _p(s, _f64p))
+    if rc != 0:
+        raise ValueError("oracle_resize_area_f64: bad arguments")
     return out
 
 

@@ -21,6 +21,8 @@
  *     weights and border as the affine warp;
  *   - a replicate-border variant of both warps (taps outside the image read the
  *     nearest edge pixel instead of zero);
+ *   - area (antialiased) downscale: each output pixel the exact overlap-
+ *     weighted mean of the source pixels its footprint covers;
  *   - Sobel 3x3 gradient magnitude (Sec. V: the robotics example's
  *     imgproc::filter::sobel(&img, &mut out, 3), RGB8 in, Gray8 out).
  *
@@ -529,5 +531,64 @@ int oracle_sobel(const uint8_t *src, long H, long W, long C, float *out_f32, uin
             if (out_u8) out_u8[y * W + x] = (uint8_t)floorf(m + 0.5f);
         }
     }
+    return ORACLE_OK;
+}
+
+/* ======================================================================== */
+/* Area (antialiased) downscale, u8 source, C = 1 or 3, w <= W, h <= H.      */
+/* Output pixel (x, y) covers the source rectangle [x W/w, (x+1) W/w) x      */
+/* [y H/h, (y+1) H/h) (source pixel i covers [i, i+1)); its value is the    */
+/* mean of the source over it, each pixel weighted by its overlap area.    */
+/* In units of 1/w (1/h) of a pixel the overlaps are integers:              */
+/*   ax(i) = max(0, min((x+1) W, (i+1) w) - max(x W, i w)),  sum_i ax = W,  */
+/* likewise ay(j) (sum = H), and                                            */
+/*   S = sum_j ay(j) sum_i ax(i) p(j, i)        (exact, 64-bit)             */
+/*   u8  = floor((2 S + W H) / (2 W H))         (mean rounded half up)      */
+/*   f64 = (S / (W H) / 255 - mean) / std.                                  */
+/* ======================================================================== */
+static long long area_sum(const uint8_t *src, long H, long W, long C, long h, long w, long x, long y, long c)
+{
+    const long long xa = (long long)x * W, xb = (long long)(x + 1) * W;
+    const long long ya = (long long)y * H, yb = (long long)(y + 1) * H;
+    long long S = 0;
+    for (long j = (long)(ya / h); j < H && (long long)j * h < yb; ++j) {
+        long long ay = (yb < (long long)(j + 1) * h ? yb : (long long)(j + 1) * h) -
+                       (ya > (long long)j * h ? ya : (long long)j * h);
+        if (ay <= 0) continue;
+        long long row = 0;
+        for (long i = (long)(xa / w); i < W && (long long)i * w < xb; ++i) {
+            long long ax = (xb < (long long)(i + 1) * w ? xb : (long long)(i + 1) * w) -
+                           (xa > (long long)i * w ? xa : (long long)i * w);
+            if (ax > 0) row += ax * src[(j * W + i) * C + c];
+        }
+        S += ay * row;
+    }
+    return S;
+}
+
+int oracle_resize_area_u8(const uint8_t *src, long H, long W, long C, uint8_t *dst, long h, long w)
+{
+    if (H < 1 || W < 1 || h < 1 || w < 1 || h > H || w > W || (C != 1 && C != 3)) return ORACLE_BAD;
+    const long long WH = (long long)W * H;
+    for (long y = 0; y < h; ++y)
+        for (long x = 0; x < w; ++x)
+            for (long c = 0; c < C; ++c) {
+                const long long S = area_sum(src, H, W, C, h, w, x, y, c);
+                dst[(y * w + x) * C + c] = (uint8_t)((2 * S + WH) / (2 * WH));
+            }
+    return ORACLE_OK;
+}
+
+int oracle_resize_area_f64(const uint8_t *src, long H, long W, long C, double *dst, long h, long w,
+                           const double *mean, const double *stdv)
+{
+    if (H < 1 || W < 1 || h < 1 || w < 1 || h > H || w > W || (C != 1 && C != 3)) return ORACLE_BAD;
+    const double WH = (double)W * (double)H;
+    for (long y = 0; y < h; ++y)
+        for (long x = 0; x < w; ++x)
+            for (long c = 0; c < C; ++c) {
+                const long long S = area_sum(src, H, W, C, h, w, x, y, c);
+                dst[(y * w + x) * C + c] = ((double)S / WH / 255.0 - mean[c]) / stdv[c];
+            }
     return ORACLE_OK;
 }

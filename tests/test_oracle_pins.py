@@ -584,3 +584,57 @@ def test_replicate_equals_zero_border_inside_and_fills_outside():
                 and math.floor(sy) + 1 < H
     np.testing.assert_array_equal(r[inside], z[inside])
     assert r[~inside].any() and (r[~inside] != z[~inside]).any()
+
+
+# ---------------------------------------------------------------------------
+# Area (antialiased) downscale
+# ---------------------------------------------------------------------------
+def test_area_same_size_is_identity():
+    img = inputs.uniform_image(150, 13, 17, 3)
+    np.testing.assert_array_equal(oracle.resize_area_u8(img, 13, 17), img)
+
+
+@pytest.mark.parametrize("ky,kx", [(2, 2), (3, 5), (4, 1), (17, 17)])
+def test_area_integer_factor_is_the_block_mean_rounded_half_up(ky, kx):
+    h, w = 5, 4
+    img = inputs.uniform_image(151, h * ky, w * kx, 3)
+    blocks = img.reshape(h, ky, w, kx, 3).astype(np.int64).sum(axis=(1, 3))
+    n = ky * kx
+    ref = (2 * blocks + n) // (2 * n)
+    np.testing.assert_array_equal(oracle.resize_area_u8(img, h, w), ref)
+    t = torch.from_numpy(img.transpose(2, 0, 1)[None].astype(np.float64) / 255.0)
+    pooled = F.avg_pool2d(t, (ky, kx))[0].numpy().transpose(1, 2, 0)
+    np.testing.assert_allclose(oracle.resize_area_f64(img, h, w), pooled, atol=1e-12)
+
+
+def test_area_brute_force_exact_overlaps():
+    rng = np.random.default_rng(152)
+    for _ in range(10):
+        H, W = (int(v) for v in rng.integers(2, 24, 2))
+        h, w = int(rng.integers(1, H + 1)), int(rng.integers(1, W + 1))
+        img = inputs.uniform_image(int(rng.integers(1 << 30)), H, W, 1)
+        got = oracle.resize_area_u8(img, h, w)
+        gotf = oracle.resize_area_f64(img, h, w)
+        for y in range(h):
+            for x in range(w):
+                fx0, fx1 = Fraction(x * W, w), Fraction((x + 1) * W, w)
+                fy0, fy1 = Fraction(y * H, h), Fraction((y + 1) * H, h)
+                acc = Fraction(0)
+                for j in range(H):
+                    oy = min(fy1, j + 1) - max(fy0, j)
+                    if oy <= 0:
+                        continue
+                    for i in range(W):
+                        ox = min(fx1, i + 1) - max(fx0, i)
+                        if ox > 0:
+                            acc += ox * oy * int(img[j, i, 0])
+                mean = acc / ((fx1 - fx0) * (fy1 - fy0))
+                assert got[y, x, 0] == math.floor(mean + Fraction(1, 2))
+                assert abs(gotf[y, x, 0] - float(mean) / 255.0) < 1e-12
+
+
+def test_area_of_a_constant_image_is_the_constant_and_preserves_the_mean():
+    np.testing.assert_array_equal(oracle.resize_area_u8(np.full((37, 53, 3), 201, np.uint8), 11, 7), 201)
+    img = inputs.uniform_image(153, 60, 90, 3)
+    f = oracle.resize_area_f64(img, 7, 13)                # the footprints tile the source exactly
+    np.testing.assert_allclose(f.mean(axis=(0, 1)), img.reshape(-1, 3).mean(0) / 255.0, rtol=1e-12)
