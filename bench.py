@@ -308,9 +308,10 @@ def serving_compare(torch, kr, dev, rates=(2000, 5000, 10000, 20000, 40000, 8000
 def next_rows(torch, kr, dev, imgs_dev, peak, reps=50):
     """The widening rows on the same frames, each one launch over the batch: nearest-neighbour
     resize -> 1280x720, horizontal flip, perspective warp (per-frame homographies, u8), Sobel
-    3x3 magnitude of the frames' gray (f32 out), the u8 affine warp with the replicated border.
+    3x3 magnitude of the frames' gray (f32 out), the u8 affine warp with the replicated border,
+    area downscales (-> 1280x720 u8; 16 x 3840x2160 -> 224x224 normalised planar f32).
     Algorithmic bytes = output + distinct source pixels read (nearest: distinct source rows x
-    distinct source columns; flip, Sobel: every pixel; warps: the oracle's touched bitmaps)."""
+    distinct source columns; flip, Sobel, area: every pixel; warps: the oracle's touched bitmaps)."""
     n, H, W, C = imgs_dev.shape
     lib = kr.load()
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
@@ -319,28 +320,41 @@ def next_rows(torch, kr, dev, imgs_dev, peak, reps=50):
     Pp = P.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     pp = kr.post()
     prep = kr.post(border="replicate")
+    # the strong-downscale case: 16 uniform 3840x2160 frames -> 224x224 normalised, planar
+    src4k = torch.from_numpy(np.stack([inputs.uniform_image(700 + i, 2160, 3840, 3) for i in range(16)])).to(dev)
+    s4k = kr.image(src4k)
+    pnorm = kr.post(mean=MEAN, std=STD)
     A = np.ascontiguousarray(inputs.bench_matrices(n).reshape(-1), dtype=np.float32)
     Ap = A.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     outs = {"resize_nearest_u8": torch.empty((n, RS_H, RS_W, C), dtype=torch.uint8, device=dev),
             "flip_u8": torch.empty((n, H, W, C), dtype=torch.uint8, device=dev),
             "warp_persp_u8": torch.empty((n, H, W, C), dtype=torch.uint8, device=dev),
             "sobel_f32": torch.empty((n, H, W, 1), dtype=torch.float32, device=dev),
-            "warp_u8_replicate": torch.empty((n, H, W, C), dtype=torch.uint8, device=dev)}
-    ds = {k: kr.image(v) for k, v in outs.items()}
+            "warp_u8_replicate": torch.empty((n, H, W, C), dtype=torch.uint8, device=dev),
+            "resize_area_u8": torch.empty((n, RS_H, RS_W, C), dtype=torch.uint8, device=dev),
+            "resize_area_16x4k_224_f32_chw": torch.empty((16, 3, 224, 224), dtype=torch.float32, device=dev)}
+    ds = {k: kr.image(v, "chw" if k.endswith("chw") else "hwc") for k, v in outs.items()}
+    d224 = ds["resize_area_16x4k_224_f32_chw"]
     calls = {"resize_nearest_u8": lambda: lib.kr_resize_nearest(ctypes.byref(s), ctypes.byref(ds["resize_nearest_u8"]), st),
              "flip_u8": lambda: lib.kr_flip_horizontal(ctypes.byref(s), ctypes.byref(ds["flip_u8"]), st),
              "warp_persp_u8": lambda: lib.kr_warp_perspective(ctypes.byref(s), ctypes.byref(ds["warp_persp_u8"]), Pp,
                                                               ctypes.byref(pp), st),
              "sobel_f32": lambda: lib.kr_sobel(ctypes.byref(s), ctypes.byref(ds["sobel_f32"]), 3, st),
              "warp_u8_replicate": lambda: lib.kr_warp_affine(ctypes.byref(s), ctypes.byref(ds["warp_u8_replicate"]),
-                                                             Ap, ctypes.byref(prep), st)}
+                                                             Ap, ctypes.byref(prep), st),
+             "resize_area_u8": lambda: lib.kr_resize_area(ctypes.byref(s), ctypes.byref(ds["resize_area_u8"]),
+                                                          ctypes.byref(pp), st),
+             "resize_area_16x4k_224_f32_chw": lambda: lib.kr_resize_area(ctypes.byref(s4k), ctypes.byref(d224),
+                                                                         ctypes.byref(pnorm), st)}
     rows = len({((2 * y + 1) * H) // (2 * RS_H) for y in range(RS_H)})
     cols = len({((2 * x + 1) * W) // (2 * RS_W) for x in range(RS_W)})
     touched = json.load(open(os.path.join(ROOT, "tests", "golden", "bench_touched.json")))["per_op"]
     alg = {"resize_nearest_u8": n * (RS_H * RS_W * C + rows * cols * C), "flip_u8": n * 2 * H * W * C,
            "warp_persp_u8": n * H * W * C + sum(touched["warp_persp_u8"]["touched_bytes"][:n]),
            "sobel_f32": n * H * W * (C + 4),
-           "warp_u8_replicate": n * H * W * C + sum(touched["warp_u8_replicate"]["touched_bytes"][:n])}
+           "warp_u8_replicate": n * H * W * C + sum(touched["warp_u8_replicate"]["touched_bytes"][:n]),
+           "resize_area_u8": n * (H * W * C + RS_H * RS_W * C),
+           "resize_area_16x4k_224_f32_chw": 16 * (2160 * 3840 * 3 + 224 * 224 * 3 * 4)}
     res = {}
     for name, fn in calls.items():
         for _ in range(3):
@@ -354,9 +368,10 @@ def next_rows(torch, kr, dev, imgs_dev, peak, reps=50):
         b.synchronize()
         ms = a.elapsed_time(b) / reps
         gbs = alg[name] / (ms * 1e-3) / 1e9
+        o = outs[name]
+        opx = o.shape[0] * (o.shape[2] * o.shape[3] if name.endswith("chw") else o.shape[1] * o.shape[2])
         res[name] = {"ms": round(ms, 4), "alg_bytes": alg[name], "GB_s": round(gbs, 1),
-                     "frac_of_measured_hbm": round(gbs / peak, 3),
-                     "gpx_s": round(n * outs[name].shape[1] * outs[name].shape[2] / (ms * 1e-3) / 1e9, 1)}
+                     "frac_of_measured_hbm": round(gbs / peak, 3), "gpx_s": round(opx / (ms * 1e-3) / 1e9, 1)}
     return res
 
 

@@ -173,6 +173,20 @@ kr_status kr_resize_nearest(const kr_image_t *src, const kr_image_t *dst, kr_str
 kr_status kr_flip_horizontal(const kr_image_t *src, const kr_image_t *dst, kr_stream_t stream);
 
 /*
+ * Area (antialiased) downscale (a variant of the resize for strong reductions
+ * such as 3840x2160 -> 224x224, where 4-tap bilinear aliases; the paper names
+ * downsizing, Sec. III, without a convention). Output pixel (x, y) is the
+ * mean of the source over [x W/w, (x+1) W/w) x [y H/h, (y+1) H/h), each
+ * source pixel weighted by its overlap area (exact integer weights); u8 dst:
+ * that mean rounded half up; f32 dst: mean / 255, then the fused normalise.
+ * src: u8 HWC C = 1 or 3. dst: same channels and batch (no KR_GRAY),
+ * w <= W and h <= H (else KR_ERR_INVALID_ARG). KR_ERR_UNSUPPORTED when the
+ * footprint of 64 output columns exceeds 96 KB of shared memory (a reduction
+ * of several hundred times along both axes at once).
+ */
+kr_status kr_resize_area(const kr_image_t *src, const kr_image_t *dst, const kr_post_t *post, kr_stream_t stream);
+
+/*
  * Sobel gradient magnitude (Sec. V: the robotics example calls
  * imgproc::filter::sobel(&img, &mut out, 3) on an RGB8 image into a Gray8
  * image; the paper gives no formula). ksize must be 3 (KR_ERR_UNSUPPORTED

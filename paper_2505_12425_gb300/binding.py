@@ -97,6 +97,7 @@ def load():
         lib.kr_rgb_to_gray.argtypes = [P(KrImage), P(KrImage), ctypes.c_void_p]
         lib.kr_resize_nearest.argtypes = [P(KrImage), P(KrImage), ctypes.c_void_p]
         lib.kr_sobel.argtypes = [P(KrImage), P(KrImage), ctypes.c_int32, ctypes.c_void_p]
+        lib.kr_resize_area.argtypes = [P(KrImage), P(KrImage), P(KrPost), ctypes.c_void_p]
         lib.kr_warp_perspective.argtypes = [P(KrImage), P(KrImage), P(ctypes.c_float), P(KrPost), ctypes.c_void_p]
         lib.kr_flip_horizontal.argtypes = [P(KrImage), P(KrImage), ctypes.c_void_p]
         lib.kr_batch_workspace_size.argtypes = [ctypes.c_int32]
@@ -120,7 +121,7 @@ def load():
         lib.kr_shutdown.argtypes = []
         lib.kr_shutdown.restype = None
         for f in ("kr_resize_bilinear", "kr_warp_affine", "kr_warp_perspective", "kr_rgb_to_gray", "kr_resize_nearest",
-                  "kr_flip_horizontal", "kr_sobel", "kr_batch_submit",
+                  "kr_flip_horizontal", "kr_sobel", "kr_resize_area", "kr_batch_submit",
                   "kr_batch_submit_noalloc", "kr_serve_run", "kr_device_errors",
                   "kr_tile_config_shape", "kr_autotune_batch", "kr_autotune_save", "kr_autotune_load"):
             getattr(lib, f).restype = S
@@ -256,6 +257,13 @@ def kr_flip_horizontal(src, dst, stream=None):
     lib = load()
     s, d = image(src), image(dst)
     _check(lib.kr_flip_horizontal(ctypes.byref(s), ctypes.byref(d), _stream(stream)), "kr_flip_horizontal")
+
+
+def kr_resize_area(src, dst, mean=None, std=None, dst_layout="hwc", stream=None):
+    """Area (overlap-weighted mean) downscale of u8 HWC `src` into `dst` (u8, or f32 normalised)."""
+    lib = load()
+    s, d, p = image(src), image(dst, dst_layout), post(False, mean, std)
+    _check(lib.kr_resize_area(ctypes.byref(s), ctypes.byref(d), ctypes.byref(p), _stream(stream)), "kr_resize_area")
 
 
 def kr_sobel(src, dst, ksize=3, stream=None):

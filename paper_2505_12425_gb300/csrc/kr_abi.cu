@@ -201,6 +201,42 @@ kr_status kr_resize_nearest(const kr_image_t *src, const kr_image_t *dst, kr_str
     return KR_OK;
 }
 
+kr_status kr_resize_area(const kr_image_t *src, const kr_image_t *dst, const kr_post_t *post, kr_stream_t stream)
+{
+    OpDesc o;
+    kr_status st = build_resample(OP_RESIZE, src, dst, post, o);
+    if (st != KR_OK) return st;
+    if (o.outk == OUT_U8_GRAY || o.outk == OUT_F32_GRAY) return KR_ERR_UNSUPPORTED;
+    if (o.h > o.H || o.w > o.W) return KR_ERR_INVALID_ARG;   // a downscale (or the same size)
+    AreaDesc d;
+    d.src = o.src;
+    d.spitch = o.spitch;
+    d.sbatch = o.sbatch;
+    d.H = o.H;
+    d.W = o.W;
+    d.dst = o.dst;
+    d.dpitch = o.dpitch;
+    d.dplane = o.dplane;
+    d.dbatch = o.dbatch;
+    d.h = o.h;
+    d.w = o.w;
+    d.C = o.cin;
+    d.f32 = o.outk == OUT_F32;
+    d.chw = o.chw;
+    d.batch = o.batch;
+    for (int k = 0; k < 3; ++k) {
+        d.scale[k] = o.scale[k];
+        d.bias[k] = o.bias[k];
+    }
+    bool too_large = false;
+    cudaError_t e = launch_area(d, (cudaStream_t)stream, too_large);
+    if (e != cudaSuccess) {
+        set_last_error("kr_resize_area", e);
+        return KR_ERR_CUDA;
+    }
+    return too_large ? KR_ERR_UNSUPPORTED : KR_OK;
+}
+
 kr_status kr_sobel(const kr_image_t *src, const kr_image_t *dst, int32_t ksize, kr_stream_t stream)
 {
     kr_status st;

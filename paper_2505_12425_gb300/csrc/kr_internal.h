@@ -74,6 +74,24 @@ struct SobelDesc {
     int batch;
 };
 cudaError_t launch_sobel(const SobelDesc &d, cudaStream_t stream);
+
+// Area (antialiased) downscale: u8 HWC source (C = 1 or 3), u8 HWC or f32 HWC/CHW output of
+// the same channels, w <= W and h <= H. too_large: the footprint box of one CTA's columns
+// exceeds kAreaSmemCap (nothing launched).
+constexpr size_t kAreaSmemCap = 96 * 1024;
+struct AreaDesc {
+    const uint8_t *src;
+    int64_t spitch, sbatch;
+    int H, W;
+    uint8_t *dst;
+    int64_t dpitch, dplane, dbatch;
+    int h, w;
+    int C;
+    int f32, chw;
+    int batch;
+    float scale[3], bias[3];
+};
+cudaError_t launch_area(const AreaDesc &d, cudaStream_t stream, bool &too_large);
 cudaError_t launch_flip_h(const GatherDesc &d, cudaStream_t stream);
 
 // Shared-memory budget of one tile: region A bytes (0 = no staging) and region B bytes

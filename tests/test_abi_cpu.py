@@ -118,6 +118,14 @@ def test_perspective_rejects_bad_maps(lib):
     assert lib.kr_warp_perspective(ctypes.byref(s), ctypes.byref(_img(data=0x10001)), a, ctypes.byref(p), None) == 3
 
 
+def test_area_rejects_upscale_and_gray(lib):
+    s = _img(h=4, w=5)
+    assert lib.kr_resize_area(ctypes.byref(s), ctypes.byref(_img(data=0x900000, h=5, w=5)), None, None) == 1
+    p = kr.post(gray=True)
+    d = _img(data=0x900000, h=2, w=2, c=1)
+    assert lib.kr_resize_area(ctypes.byref(s), ctypes.byref(d), ctypes.byref(p), None) == 2
+
+
 def test_sobel_rejects_bad_arguments(lib):
     s = _img()
     d = _img(data=0x900000, c=1)

@@ -560,3 +560,37 @@ def test_ragged_batch_with_replicate_border():
     for i, ((img, M, H, W), d) in enumerate(zip(items, dsts)):
         ref = oracle.warp_u8(img, M, H, W, border="replicate" if i % 2 else "zero")
         np.testing.assert_array_equal(d.cpu().numpy(), ref)
+
+
+# ---------------------------------------------------------------------------
+# Area (antialiased) downscale
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("H,W,h,w,C", [(1080, 1920, 720, 1280, 3), (1080, 1920, 540, 960, 3), (37, 53, 11, 17, 3),
+                                       (100, 100, 33, 47, 1), (64, 64, 64, 64, 3), (1, 300, 1, 7, 3),
+                                       (300, 2, 5, 1, 1), (257, 129, 65, 97, 3)])
+def test_resize_area(H, W, h, w, C):
+    img = inputs.uniform_image(H * 3 + W, H, W, C)
+    u = Guarded((h, w, C), torch.uint8)
+    f = Guarded((h, w, C), torch.float32)
+    kr.kr_resize_area(to_dev(img), u.t)
+    kr.kr_resize_area(to_dev(img), f.t)
+    torch.cuda.synchronize()
+    u.check()
+    f.check()
+    np.testing.assert_array_equal(u.np(), oracle.resize_area_u8(img, h, w))
+    assert np.abs(f.np() - oracle.resize_area_f64(img, h, w)).max() <= F32_TOL
+
+
+def test_resize_area_16x4k_to_224_normalised_nchw():
+    n, H, W = 16, 2160, 3840
+    imgs = np.stack([inputs.uniform_image(700 + i, H, W, 3) for i in range(n)])
+    out = Guarded((n, 3, 224, 224), torch.float32)
+    kr.kr_resize_area(to_dev(imgs), out.t, mean=MEAN, std=STD, dst_layout="chw")
+    u = torch.empty((n, 224, 224, 3), dtype=torch.uint8, device=dev())
+    kr.kr_resize_area(to_dev(imgs), u)
+    torch.cuda.synchronize()
+    out.check()
+    for i in (0, 7, 15):
+        ref = oracle.resize_area_f64(imgs[i], 224, 224, mean=MEAN, std=STD)
+        assert np.abs(out.np()[i].transpose(1, 2, 0) - ref).max() <= F32_TOL
+        np.testing.assert_array_equal(u[i].cpu().numpy(), oracle.resize_area_u8(imgs[i], 224, 224))
