@@ -504,7 +504,7 @@ def run_gpu(args):
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 3),
            "steps": K_e2e}
 
-    widening = next_rows(torch, kr, dev, imgs_dev, peak)
+    widening = next_rows(torch, kr, dev, imgs_dev, peak) if not args.no_extras else None
     ragged = ragged_compare(torch, kr, dev) if not args.no_extras else None
     serving = serving_compare(torch, kr, dev, seconds=args.serve_seconds) if not args.no_extras else None
     cpu = cpu_baseline_sample() if (rank == 0 and not args.no_extras) else None
@@ -578,7 +578,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--no-extras", action="store_true", help="skip the ragged comparison and the CPU baseline")
+    ap.add_argument("--no-extras", action="store_true", help="skip the next rows, the ragged and serving comparisons and the CPU baseline")
     ap.add_argument("--clocks-dir", default=None,
                     help="directory for the raw nvidia-smi clock samples (default: a temporary one)")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="seconds of requests per serving rate")
