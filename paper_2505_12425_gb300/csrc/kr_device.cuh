@@ -407,12 +407,6 @@ __device__ __forceinline__ F2 f2_add_rm(F2 a, F2 b)
     return r;
 }
 
-// R and G of a pixel word as an exact float pair (the 2^23 trick on both lanes at once).
-__device__ __forceinline__ F2 rg_f2(uint32_t w)
-{
-    const F2 biased = f2_pack_bits(__byte_perm(w, 0x4B000000u, 0x7540), __byte_perm(w, 0x4B000000u, 0x7541));
-    return f2_sub(biased, f2_pack(8388608.f, 8388608.f));
-}
 
 // Packed 11-bit weight pair for dp2a: low half 2048 - q, high half q.
 __device__ __forceinline__ uint32_t wpair(int q) { return 2048u + (uint32_t)q * 65535u; }
@@ -540,15 +534,21 @@ __device__ __forceinline__ U8x3 hblend_pair(uint32_t p0, uint32_t p1, uint32_t w
     return o;
 }
 
-// R, G of the pair's second pixel as an exact float pair, and B of both pixels.
-template <int F>
-__device__ __forceinline__ F2 rg1_f2(uint32_t p0, uint32_t p1)
+
+// The same taps as 2^23 + byte, not yet unbiased (exact floats; differences are exact).
+__device__ __forceinline__ F2 rg_biased(uint32_t w)
 {
-    if (F == TAPS_WORDS) return rg_f2(p1);
-    const F2 biased = f2_pack_bits(__byte_perm(p0, 0x4B000000u, 0x7543), __byte_perm(p1, 0x4B000000u, 0x7540));
-    return f2_sub(biased, f2_pack(8388608.f, 8388608.f));
+    return f2_pack_bits(__byte_perm(w, 0x4B000000u, 0x7540), __byte_perm(w, 0x4B000000u, 0x7541));
 }
-template <int F> __device__ __forceinline__ float b1_f(uint32_t p1) { return byte_f(p1, F == TAPS_WORDS ? 2 : 1); }
+template <int F> __device__ __forceinline__ F2 rg1_biased(uint32_t p0, uint32_t p1)
+{
+    if (F == TAPS_WORDS) return rg_biased(p1);
+    return f2_pack_bits(__byte_perm(p0, 0x4B000000u, 0x7543), __byte_perm(p1, 0x4B000000u, 0x7540));
+}
+template <int F> __device__ __forceinline__ uint32_t b1_biased(uint32_t p1)
+{
+    return __byte_perm(p1, 0x4B000000u, F == TAPS_WORDS ? 0x7542 : 0x7541);
+}
 
 // ---------------------------------------------------------------------------
 // Per-pixel output: blend the taps and put the result into the output tile.
@@ -581,15 +581,24 @@ __device__ __forceinline__ void emit(const Job &J, const ORow &o, int c, uint32_
     } else {
         float v[3];
         if (CIN == 3) {
-            // R and G in packed f32x2 lanes, B alone: lerp along x on both rows, then along y.
+            // Lerp along x on both rows, then along y: R and G of a row in one packed f32x2
+            // pair, B alone. Taps are read as 2^23 + byte (exact); the
+            // difference of two such taps is the difference of the bytes, and only the base
+            // of each lerp is unbiased: fma(f, b - a, a) with the same operands as on bytes.
+            const F2 K = f2_pack(8388608.f, 8388608.f);
             const F2 fx2 = f2_pack(fx, fx), fy2 = f2_pack(fy, fy);
-            const F2 a = rg_f2(p00), b = rg1_f2<F>(p00, p01), cc = rg_f2(p10), d = rg1_f2<F>(p10, p11);
-            const F2 h0 = f2_fma(fx2, f2_sub(b, a), a);
-            const F2 h1 = f2_fma(fx2, f2_sub(d, cc), cc);
+            const F2 a = rg_biased(p00), b = rg1_biased<F>(p00, p01);
+            const F2 cc = rg_biased(p10), d = rg1_biased<F>(p10, p11);
+            const F2 h0 = f2_fma(fx2, f2_sub(b, a), f2_sub(a, K));
+            const F2 h1 = f2_fma(fx2, f2_sub(d, cc), f2_sub(cc, K));
             f2_unpack(f2_fma(fy2, f2_sub(h1, h0), h0), v[0], v[1]);
-            const float ab = byte_f(p00, 2), bb = b1_f<F>(p01), cb = byte_f(p10, 2), db = b1_f<F>(p11);
-            const float g0 = __fmaf_rn(fx, __fsub_rn(bb, ab), ab);
-            const float g1 = __fmaf_rn(fx, __fsub_rn(db, cb), cb);
+            const float kb = 8388608.f;
+            const float ba = __uint_as_float(__byte_perm(p00, 0x4B000000u, 0x7542));
+            const float bb = __uint_as_float(b1_biased<F>(p01));
+            const float bc = __uint_as_float(__byte_perm(p10, 0x4B000000u, 0x7542));
+            const float bd = __uint_as_float(b1_biased<F>(p11));
+            const float g0 = __fmaf_rn(fx, __fsub_rn(bb, ba), __fsub_rn(ba, kb));
+            const float g1 = __fmaf_rn(fx, __fsub_rn(bd, bc), __fsub_rn(bc, kb));
             v[2] = __fmaf_rn(fy, __fsub_rn(g1, g0), g0);
         } else {
             const float a = byte_f(p00, 0), b = byte_f(p01, 0);
