@@ -504,10 +504,10 @@ def run_gpu(args):
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 3),
            "steps": K_e2e}
 
-    widening = next_rows(torch, kr, dev, imgs_dev, peak) if not args.no_extras else None
-    ragged = ragged_compare(torch, kr, dev) if not args.no_extras else None
-    serving = serving_compare(torch, kr, dev, seconds=args.serve_seconds) if not args.no_extras else None
-    cpu = cpu_baseline_sample() if (rank == 0 and not args.no_extras) else None
+    widening = next_rows(torch, kr, dev, imgs_dev, peak, reps=args.next_reps) if args.extras != "none" else None
+    ragged = ragged_compare(torch, kr, dev) if args.extras == "all" else None
+    serving = serving_compare(torch, kr, dev, seconds=args.serve_seconds) if args.extras == "all" else None
+    cpu = cpu_baseline_sample() if (rank == 0 and args.extras == "all") else None
 
     if rank == 0:
         line = {
@@ -579,12 +579,19 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-extras", action="store_true", help="skip the next rows, the ragged and serving comparisons and the CPU baseline")
+    ap.add_argument("--extras", choices=["all", "next-rows", "none"], default="all",
+                    help="which extra measurements follow the step: all, only the next rows, or none")
+    ap.add_argument("--next-reps", type=int, default=50, help="timed launches per next row")
     ap.add_argument("--clocks-dir", default=None,
                     help="directory for the raw nvidia-smi clock samples (default: a temporary one)")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="seconds of requests per serving rate")
     ap.add_argument("--images", type=int, default=inputs.BENCH_IMAGES,
                     help="frames per step (the full workload is 32; fewer only for small profiling cases)")
     args = ap.parse_args()
+    if args.no_extras:
+        args.extras = "none"
+    if args.next_reps < 1:
+        ap.error("--next-reps must be >= 1")
     if not 1 <= args.images <= inputs.BENCH_IMAGES:
         ap.error(f"--images must be in 1..{inputs.BENCH_IMAGES}")
     if args.warmup < 3:

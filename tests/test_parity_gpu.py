@@ -351,6 +351,10 @@ NEAREST_CASES = [
     (480, 640, 240, 320, 3), (1080, 1920, 720, 1280, 3), (37, 53, 91, 17, 3), (100, 100, 33, 47, 1),
     (1, 1, 5, 7, 3), (1, 300, 1, 257, 3), (300, 1, 257, 1, 1), (64, 64, 64, 64, 3), (2160, 3840, 224, 224, 3),
     (33, 65, 130, 258, 1), (257, 129, 65, 97, 3),
+    # source rows above 48 KB take the byte-gather kernel; the others are staged whole
+    (3, 16400, 4, 301, 3), (2, 16373, 3, 20000, 3), (2, 16374, 3, 9, 3),
+    # (2x + 1) W above 2^32: the first division of a row chunk needs 64 bits
+    (2, 48000, 2, 65000, 1),
 ]
 
 
@@ -364,7 +368,8 @@ def test_resize_nearest(H, W, h, w, C):
     np.testing.assert_array_equal(out.np(), oracle.resize_nearest_u8(img, h, w))
 
 
-@pytest.mark.parametrize("H,W,C", [(1080, 1920, 3), (17, 29, 3), (1, 1, 3), (5, 301, 1), (300, 2, 3)])
+@pytest.mark.parametrize("H,W,C", [(1080, 1920, 3), (17, 29, 3), (1, 1, 3), (5, 301, 1), (300, 2, 3),
+                                   (3, 16384, 3), (3, 16385, 3), (2, 60001, 1)])
 def test_flip_horizontal(H, W, C):
     img = inputs.uniform_image(H + 3 * W, H, W, C)
     out = Guarded((H, W, C), torch.uint8)
@@ -396,6 +401,32 @@ def test_gathers_on_views_and_batches():
     for i in range(n):
         np.testing.assert_array_equal(nd[i].cpu().numpy(), oracle.resize_nearest_u8(imgs[i], 50, 63))
         np.testing.assert_array_equal(fd[i].cpu().numpy(), oracle.flip_h_u8(imgs[i]))
+
+
+@pytest.mark.parametrize("sx0,dx0", [(1, 0), (0, 3), (5, 2), (7, 7)])
+def test_gathers_on_views_with_16_byte_pitches(sx0, dx0):
+    # pitches and batch strides multiples of 16 with the first pixel at a byte phase: every row
+    # and image shares the phase, the 3-channel path with one chunk per thread runs
+    n, H, W = 3, 37, 101
+    imgs = np.stack([inputs.uniform_image(90 + i, H, W, 3) for i in range(n)])
+    big = torch.full((n, H, 112, 3), 7, dtype=torch.uint8, device=dev())
+    big[:, :, sx0:sx0 + W] = to_dev(imgs)
+    src = big[:, :, sx0:sx0 + W]
+    for name, w in (("nearest", 70), ("nearest", 150), ("flip", W)):
+        dbig = torch.full((n, 24 if name == "nearest" else H, 176, 3), CANARY_U8, dtype=torch.uint8, device=dev())
+        h = dbig.shape[1]
+        out = dbig[:, :, dx0:dx0 + w]
+        if name == "nearest":
+            kr.kr_resize_nearest(src, out)
+        else:
+            kr.kr_flip_horizontal(src, out)
+        torch.cuda.synchronize()
+        m = torch.ones(dbig.shape[:3], dtype=torch.bool, device=dev())
+        m[:, :, dx0:dx0 + w] = False
+        assert bool((dbig[m] == CANARY_U8).all()), "write outside the destination view"
+        for i in range(n):
+            want = oracle.resize_nearest_u8(imgs[i], h, w) if name == "nearest" else oracle.flip_h_u8(imgs[i])
+            np.testing.assert_array_equal(out[i].cpu().numpy(), want)
 
 
 def test_flip_equals_warp_with_the_mirror_map():
