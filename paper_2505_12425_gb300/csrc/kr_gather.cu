@@ -61,8 +61,8 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const __grid_con
     }
 }
 
-constexpr int kRowBufBytes = 48 * 1024;
-constexpr int kChunkThreadsMax = 1024;   // one staged source row, with its phase and read slack
+constexpr int kRowBufBytes = 48 * 1024;   // one staged source row with its pads and phase
+constexpr int kChunkThreadsMax = 1024;
 
 __device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
 {
@@ -151,18 +151,19 @@ struct ColMap {
     }
 };
 
-// The four output words of a 16-byte chunk whose first byte has pixel phase PH (3 channels):
-// word j starts at chunk byte 4j, i.e. pixel (PH + 4j) div 3 of the chunk's six, channel
-// (PH + 4j) mod 3, and takes its bytes from that pixel and the next one (one byte permute).
-template <int PH>
-__device__ __forceinline__ void words3(const uint32_t (&P)[6], uint32_t (&w)[4])
+// The four output words of a 16-byte chunk whose first byte has pixel phase ph (3 channels):
+// word j starts at chunk byte 4j, i.e. pixel (ph + 4j) div 3 of the chunk's six P[0..5], channel
+// (ph + 4j) mod 3, and takes its bytes from that pixel and the next one (one byte permute).
+__device__ __forceinline__ void words3(const uint32_t (&P)[6], int ph, uint32_t (&w)[4])
 {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        constexpr unsigned seq = 0x654210u;   // byte sources: P.c0 P.c1 P.c2 Q.c0 Q.c1 Q.c2
-        const int i = (PH + 4 * j) / 3, ph = (PH + 4 * j) % 3;
-        w[j] = __byte_perm(P[i], P[i + 1], (seq >> (4 * ph)) & 0xFFFFu);
-    }
+    constexpr unsigned seq = 0x654210u;   // byte sources: P.c0 P.c1 P.c2 Q.c0 Q.c1 Q.c2
+    const unsigned sel0 = (seq >> (4 * ph)) & 0xFFFFu;
+    const unsigned sel1 = (seq >> (4 * (ph < 2 ? ph + 1 : 0))) & 0xFFFFu;
+    const unsigned sel2 = (seq >> (4 * (ph == 0 ? 2 : ph - 1))) & 0xFFFFu;
+    w[0] = __byte_perm(P[0], P[1], sel0);
+    w[1] = ph < 2 ? __byte_perm(P[1], P[2], sel1) : __byte_perm(P[2], P[3], sel1);
+    w[2] = ph == 0 ? __byte_perm(P[2], P[3], sel2) : __byte_perm(P[3], P[4], sel2);
+    w[3] = __byte_perm(P[4], P[5], sel0);
 }
 
 template <int C, bool NEAREST>
@@ -212,7 +213,8 @@ __global__ void __launch_bounds__(kGatherThreads, 8) row_gather_kernel(const __g
         cp_async_wait(nbuf - 1);   // this row's copies are done (later rows' may be in flight)
         __syncthreads();
         slot = slot + 1 == nbuf ? 0 : slot + 1;
-        const uint8_t *s0 = s + ((uintptr_t)row_of(y) & 15);   // the staged row's byte 0
+        const int r0 = (int)((uintptr_t)row_of(y) & 15);   // staged offset of the row's byte 0
+        const uint8_t *s0 = s + r0;
         uint8_t *d = dst + (int64_t)y * p.dpitch;
         const int dph = (int)((uintptr_t)d & 15);
         const int nchd = (dph + dbytes + 15) >> 4;
@@ -226,19 +228,13 @@ __global__ void __launch_bounds__(kGatherThreads, 8) row_gather_kernel(const __g
                 uint32_t P[6];
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
-                    const int a = 3 * cm.sx(c);
-                    const uint8_t *q = s0 + a;
-                    const int sh = (int)((uintptr_t)q & 3);
-                    const uint8_t *qa = q - sh;
+                    const int a = r0 + 3 * cm.sx(c);
+                    const int sh = a & 3;
+                    const uint8_t *qa = s + (a - sh);
                     P[i] = __funnelshift_r(lds32(qa), lds32(qa + 4), 8 * sh);
                     cm.next(c);
                 }
-                if (ph == 0)
-                    words3<0>(P, w);
-                else if (ph == 1)
-                    words3<1>(P, w);
-                else
-                    words3<2>(P, w);
+                words3(P, ph, w);
             } else {
                 auto c = cm.at(b0);
 #pragma unroll
@@ -361,6 +357,78 @@ __global__ void __launch_bounds__(kChunkThreadsMax, 2) row_gather3_kernel(const 
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+// The flip of 3-channel rows whose destination rows start on 16-byte boundaries (destination
+// pitch, batch stride and base multiples of 16): thread g of a row writes output pixels
+// 16g .. 16g+15 (48 bytes, three aligned 16-byte stores) from source pixels W-16-16g ..
+// W-1-16g, a 48-byte window whose 16-byte phase is the same for every group of the row. The
+// window is read as three or four aligned 16-byte loads and funnel-shifted by that phase, then
+// reversed four pixels (12 bytes, four byte permutes) at a time. Groups whose loads would
+// leave the source row (at some phases the row's first and last groups) and a partial last
+// group copy pixel by pixel. No shared memory: loads and stores are independent per thread.
+__global__ void __launch_bounds__(256) flip3_kernel(const __grid_constant__ GatherParams p)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= (p.W + 15) >> 4) return;
+    const uint8_t *srow = p.src + (int64_t)blockIdx.z * p.sbatch + (int64_t)blockIdx.y * p.spitch;
+    uint8_t *drow = p.dst + (int64_t)blockIdx.z * p.dbatch + (int64_t)blockIdx.y * p.dpitch;
+    const int sbytes = 3 * p.W;
+    const int x0 = 16 * g;                                  // first output pixel of the group
+    const int lo = 3 * (p.W - 16 - x0);                     // window start in the row (< 0: partial group)
+    const int u = (int)(((uintptr_t)srow + (uintptr_t)(intptr_t)lo) & 15);
+    const int la = lo - u;                                  // first aligned block of the window
+    const int nb = u == 0 ? 3 : 4;
+    if (x0 + 16 <= p.W && la >= 0 && la + 16 * nb <= sbytes) {
+        const uint4 *q = reinterpret_cast<const uint4 *>(srow + la);
+        const uint4 b0 = __ldg(q), b1 = __ldg(q + 1), b2 = __ldg(q + 2);
+        const uint4 b3 = nb == 4 ? __ldg(q + 3) : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t V[16] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w,
+                                b2.x, b2.y, b2.z, b2.w, b3.x, b3.y, b3.z, b3.w};
+        const int sh = 8 * (u & 3);
+        uint32_t A[12];   // the window: source pixels S0 .. S15, S_m at bytes 3m .. 3m+2
+        switch (u >> 2) {
+        case 0:
+#pragma unroll
+            for (int j = 0; j < 12; ++j) A[j] = __funnelshift_r(V[j], V[j + 1], sh);
+            break;
+        case 1:
+#pragma unroll
+            for (int j = 0; j < 12; ++j) A[j] = __funnelshift_r(V[j + 1], V[j + 2], sh);
+            break;
+        case 2:
+#pragma unroll
+            for (int j = 0; j < 12; ++j) A[j] = __funnelshift_r(V[j + 2], V[j + 3], sh);
+            break;
+        default:
+#pragma unroll
+            for (int j = 0; j < 12; ++j) A[j] = __funnelshift_r(V[j + 3], V[j + 4], sh);
+            break;
+        }
+        // output pixels 4k .. 4k+3 are S_{15-4k} .. S_{12-4k}: the 12 window bytes of words
+        // x0 x1 x2 = A[9-3k] A[10-3k] A[11-3k], pixel order reversed, channel order kept
+        uint32_t o[12];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t x0w = A[9 - 3 * k], x1w = A[10 - 3 * k], x2w = A[11 - 3 * k];
+            o[3 * k] = __byte_perm(x1w, x2w, 0x2765);                         // S3.c0-2, S2.c0
+            o[3 * k + 1] = __byte_perm(__byte_perm(x1w, x2w, 0x0043), x0w, 0x3710);   // S2.c1-2, S1.c0-1
+            o[3 * k + 2] = __byte_perm(x0w, x1w, 0x2105);                     // S1.c2, S0.c0-2
+        }
+        uint4 *d = reinterpret_cast<uint4 *>(drow + 48 * g);
+        d[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        d[1] = make_uint4(o[4], o[5], o[6], o[7]);
+        d[2] = make_uint4(o[8], o[9], o[10], o[11]);
+    } else {
+        const int n = min(16, p.W - x0);
+        for (int i = 0; i < n; ++i) {
+            const uint8_t *s = srow + 3 * (p.W - 1 - x0 - i);
+            uint8_t *d = drow + 3 * (x0 + i);
+            d[0] = __ldg(s);
+            d[1] = __ldg(s + 1);
+            d[2] = __ldg(s + 2);
+        }
+    }
+}
+
 template <bool NEAREST>
 cudaError_t launch_gather(const GatherDesc &d, cudaStream_t stream)
 {
@@ -375,6 +443,14 @@ cudaError_t launch_gather(const GatherDesc &d, cudaStream_t stream)
     p.dbatch = d.dbatch;
     p.h = d.h;
     p.w = d.w;
+    if (!NEAREST && d.C == 3 && d.dpitch % 16 == 0 && ((uintptr_t)d.dst & 15) == 0 &&
+        (d.batch == 1 || d.dbatch % 16 == 0) && d.H <= 65535 && d.batch <= 65535) {
+        const int ng = (d.W + 15) / 16;
+        const int bx = std::min(256, 32 * ((ng + 31) / 32));
+        const dim3 g3((ng + bx - 1) / bx, d.H, d.batch);
+        flip3_kernel<<<g3, bx, 0, stream>>>(p);
+        return cudaGetLastError();
+    }
     // a staged row: up to 15 bytes of phase, the row, and 8 bytes that word reads may touch
     const long long buf = ((long long)d.W * d.C + 15 + 8 + 15) & ~15LL;
     if (buf <= kRowBufBytes && d.batch <= 65535) {

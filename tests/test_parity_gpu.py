@@ -352,7 +352,7 @@ NEAREST_CASES = [
     (1, 1, 5, 7, 3), (1, 300, 1, 257, 3), (300, 1, 257, 1, 1), (64, 64, 64, 64, 3), (2160, 3840, 224, 224, 3),
     (33, 65, 130, 258, 1), (257, 129, 65, 97, 3),
     # source rows above 48 KB take the byte-gather kernel; the others are staged whole
-    (3, 16400, 4, 301, 3), (2, 16373, 3, 20000, 3), (2, 16374, 3, 9, 3),
+    (3, 16400, 4, 301, 3), (2, 16371, 3, 20000, 3), (2, 16372, 3, 9, 3),
     # (2x + 1) W above 2^32: the first division of a row chunk needs 64 bits
     (2, 48000, 2, 65000, 1),
 ]
@@ -369,7 +369,7 @@ def test_resize_nearest(H, W, h, w, C):
 
 
 @pytest.mark.parametrize("H,W,C", [(1080, 1920, 3), (17, 29, 3), (1, 1, 3), (5, 301, 1), (300, 2, 3),
-                                   (3, 16384, 3), (3, 16385, 3), (2, 60001, 1)])
+                                   (3, 16371, 3), (3, 16372, 3), (2, 49114, 1), (2, 49115, 1), (2, 60001, 1)])
 def test_flip_horizontal(H, W, C):
     img = inputs.uniform_image(H + 3 * W, H, W, C)
     out = Guarded((H, W, C), torch.uint8)
