@@ -76,8 +76,8 @@ struct SobelDesc {
 cudaError_t launch_sobel(const SobelDesc &d, cudaStream_t stream);
 
 // Area (antialiased) downscale: u8 HWC source (C = 1 or 3), u8 HWC or f32 HWC/CHW output of
-// the same channels, w <= W and h <= H. too_large: the footprint box of one CTA's columns
-// exceeds kAreaSmemCap (nothing launched).
+// the same channels, w <= W and h <= H. too_large: two ring slots of one output column's
+// source footprint row exceed kAreaSmemCap (nothing launched).
 constexpr size_t kAreaSmemCap = 96 * 1024;
 struct AreaDesc {
     const uint8_t *src;

@@ -126,6 +126,14 @@ def test_area_rejects_upscale_and_gray(lib):
     assert lib.kr_resize_area(ctypes.byref(s), ctypes.byref(d), ctypes.byref(p), None) == 2
 
 
+def test_area_footprint_too_wide_is_unsupported(lib):
+    # one output column over 65535 source columns: two ring slots of its footprint row exceed
+    # the shared-memory budget, reported before anything is launched
+    s = _img(h=1, w=65535)
+    d = _img(data=0x900000, h=1, w=1)
+    assert lib.kr_resize_area(ctypes.byref(s), ctypes.byref(d), None, None) == 2
+
+
 def test_sobel_rejects_bad_arguments(lib):
     s = _img()
     d = _img(data=0x900000, c=1)

@@ -598,7 +598,11 @@ def test_ragged_batch_with_replicate_border():
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("H,W,h,w,C", [(1080, 1920, 720, 1280, 3), (1080, 1920, 540, 960, 3), (37, 53, 11, 17, 3),
                                        (100, 100, 33, 47, 1), (64, 64, 64, 64, 3), (1, 300, 1, 7, 3),
-                                       (300, 2, 5, 1, 1), (257, 129, 65, 97, 3)])
+                                       (300, 2, 5, 1, 1), (257, 129, 65, 97, 3),
+                                       # strips of fewer than 256 columns (a footprint row of 6667 pixels)
+                                       (2, 20000, 2, 3, 3),
+                                       # 64-bit sums: 255 W H >= 2^32
+                                       (4100, 4100, 3, 5, 1)])
 def test_resize_area(H, W, h, w, C):
     img = inputs.uniform_image(H * 3 + W, H, W, C)
     u = Guarded((h, w, C), torch.uint8)
@@ -610,6 +614,24 @@ def test_resize_area(H, W, h, w, C):
     f.check()
     np.testing.assert_array_equal(u.np(), oracle.resize_area_u8(img, h, w))
     assert np.abs(f.np() - oracle.resize_area_f64(img, h, w)).max() <= F32_TOL
+
+
+def test_resize_area_on_views_and_batches():
+    # odd pitch and offset (every staged row has its own 16-byte phase), several strips and bands
+    n, H, W, h, w = 3, 91, 700, 40, 300
+    imgs = np.stack([inputs.uniform_image(60 + i, H, W, 3) for i in range(n)])
+    big = torch.full((n, H + 2, W + 5, 3), 9, dtype=torch.uint8, device=dev())
+    big[:, 1:1 + H, 3:3 + W] = to_dev(imgs)
+    src = big[:, 1:1 + H, 3:3 + W]
+    dbig = torch.full((n, h + 2, w + 3, 3), CANARY_U8, dtype=torch.uint8, device=dev())
+    out = dbig[:, 1:1 + h, 2:2 + w]
+    kr.kr_resize_area(src, out)
+    torch.cuda.synchronize()
+    m = torch.ones(dbig.shape[:3], dtype=torch.bool, device=dev())
+    m[:, 1:1 + h, 2:2 + w] = False
+    assert bool((dbig[m] == CANARY_U8).all()), "write outside the destination view"
+    for i in range(n):
+        np.testing.assert_array_equal(out[i].cpu().numpy(), oracle.resize_area_u8(imgs[i], h, w))
 
 
 def test_resize_area_16x4k_to_224_normalised_nchw():
