@@ -1,19 +1,21 @@
 // Sobel 3x3 gradient magnitude (u8 HWC source, 1 or 3 channels; 3 channels are first the
 // u8 BT.601 gray), replicated border, f32 or u8 single-channel output:
 //   m = sqrt(gx^2 + gy^2) / 8 (normalised kernels), u8 = floor(m + 1/2).
-// One CTA of 256 threads per 64 x 32 output tile: the tile's gray values with a one-pixel
-// halo (border replicated) are staged in shared memory; each thread then slides a 3 x 3
-// window down 4 rows of 2 columns, keeping per row the horizontal smooth (v0 + 2 v1 + v2)
-// and difference (v2 - v0), so each output reads 3 new shared-memory bytes.
+// A thread owns 4 output columns x0 .. x0+3 of a run of 16 output rows and walks down the
+// run: per source row it forms the gray values of the 6 source pixels x0-1 .. x0+4, their
+// horizontal smooths (v0 + 2 v1 + v2) and differences (v2 - v0), and keeps the last three
+// rows' in registers. Inside the row (3 channels) the 18 source bytes are read as aligned
+// words (their phase is the same for every thread of a row, so one switch picks the byte
+// positions) and each gray is one dp2a; at the left and right edges pixels are read one by
+// one with the column clamped. No shared memory.
 #include "kr_device.cuh"
 #include "kr_internal.h"
 
 namespace kr {
 namespace {
 
-constexpr int kSW = 64, kSH = 32;                     // output tile
-constexpr int kHW = kSW + 2, kHH = kSH + 2;           // staged halo box
-constexpr int kRowsPerThread = kSH / kWarps;          // 4
+constexpr int kGroup = 4;   // output columns per thread
+constexpr int kRun = 16;    // output rows per thread
 
 struct SobelParams {
     const uint8_t *src;
@@ -23,58 +25,110 @@ struct SobelParams {
     int64_t dpitch, dbatch;
 };
 
+// gray of the 3-channel pixel in bytes 0..2 of P: (4899 R + 9617 G + 1868 B + 8192) >> 14
+__device__ __forceinline__ int gray_word(uint32_t P)
+{
+    return (int)(__dp2a_lo(4899u | (9617u << 16), P, 8192u + 1868u * ((P >> 16) & 255u)) >> 14);
+}
+
+// the six pixels of a row starting at byte SH of the words w[0..5]
+template <int SH>
+__device__ __forceinline__ void gray6_words(const uint32_t (&w)[6], int (&gv)[6])
+{
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const int o = SH + 3 * i;
+        gv[i] = gray_word(__funnelshift_r(w[o >> 2], w[(o >> 2) + 1], 8 * (o & 3)));
+    }
+}
+
 template <int C, bool F32>
 __global__ void __launch_bounds__(kThreads) sobel_kernel(const __grid_constant__ SobelParams p)
 {
-    __shared__ uint8_t g[kHH][kHW + 2];
-    const int tx0 = blockIdx.x * kSW, ty0 = blockIdx.y * kSH;
+    const int x0 = kGroup * (int)(blockIdx.x * kThreads + threadIdx.x);
+    if (x0 >= p.W) return;
+    const int y0 = blockIdx.y * kRun, ny = min(kRun, p.H - y0);
     const uint8_t *src = p.src + (int64_t)blockIdx.z * p.sbatch;
-    // stage the gray halo box, border replicated
-    for (int i = threadIdx.x; i < kHH * kHW; i += kThreads) {
-        const int hy = i / kHW, hx = i - hy * kHW;
-        const int y = min(max(ty0 + hy - 1, 0), p.H - 1), x = min(max(tx0 + hx - 1, 0), p.W - 1);
-        const uint8_t *s = src + (int64_t)y * p.spitch + (int64_t)x * C;
-        g[hy][hx] = C == 3 ? (uint8_t)gray_u8(__ldg(s), __ldg(s + 1), __ldg(s + 2)) : __ldg(s);
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r0 = warp * kRowsPerThread;
     uint8_t *dst = p.dst + (int64_t)blockIdx.z * p.dbatch;
+    // word reads stay inside the row: its bytes from 3 (x0 - 2) to 3 (x0 + 6) - 1
+    const bool fast = C == 3 && x0 >= 2 && x0 + 5 <= p.W - 1;
+    auto gray6 = [&](int y, int (&gv)[6]) {
+        const uint8_t *row = src + (int64_t)min(max(y, 0), p.H - 1) * p.spitch;
+        if (fast) {
+            const uint8_t *a = row + 3 * (x0 - 1);
+            const int sh = (int)((uintptr_t)a & 3);
+            const uint32_t *wp = reinterpret_cast<const uint32_t *>(a - sh);
+            uint32_t w[6];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const int c = lane + 32 * j;             // output column in the tile; halo column c + 1
-        const int x = tx0 + c;
-        if (x >= p.W) continue;
-        // rows r0 - 1 and r0 of the output are halo rows r0 and r0 + 1
-        int d_a, h_a, d_b, h_b;
-        {
-            const int v0 = g[r0][c], v1 = g[r0][c + 1], v2 = g[r0][c + 2];
-            d_a = v2 - v0;
-            h_a = v0 + 2 * v1 + v2;
-        }
-        {
-            const int v0 = g[r0 + 1][c], v1 = g[r0 + 1][c + 1], v2 = g[r0 + 1][c + 2];
-            d_b = v2 - v0;
-            h_b = v0 + 2 * v1 + v2;
-        }
-#pragma unroll
-        for (int k = 0; k < kRowsPerThread; ++k) {
-            const int hr = r0 + k + 2;
-            const int v0 = g[hr][c], v1 = g[hr][c + 1], v2 = g[hr][c + 2];
-            const int d_c = v2 - v0, h_c = v0 + 2 * v1 + v2;
-            const int gx = d_a + 2 * d_b + d_c;
-            const int gy = h_c - h_a;
-            const int y = ty0 + r0 + k;
-            if (y < p.H) {
-                const float m = __fmul_rn(__fsqrt_rn((float)(gx * gx + gy * gy)), 0.125f);
-                uint8_t *row = dst + (int64_t)y * p.dpitch;
-                if (F32)
-                    reinterpret_cast<float *>(row)[x] = m;
-                else
-                    row[x] = (uint8_t)floorf(__fadd_rn(m, 0.5f));
+            for (int t = 0; t < 6; ++t) w[t] = 4 * t < sh + 18 ? __ldg(wp + t) : 0u;
+            switch (sh) {
+            case 0: gray6_words<0>(w, gv); break;
+            case 1: gray6_words<1>(w, gv); break;
+            case 2: gray6_words<2>(w, gv); break;
+            default: gray6_words<3>(w, gv); break;
             }
-            d_a = d_b; h_a = h_b;
-            d_b = d_c; h_b = h_c;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                const uint8_t *s = row + (int64_t)min(max(x0 - 1 + i, 0), p.W - 1) * C;
+                gv[i] = C == 3 ? (int)gray_u8(__ldg(s), __ldg(s + 1), __ldg(s + 2)) : (int)__ldg(s);
+            }
+        }
+    };
+    int da[4], ha[4], db[4], hb[4];
+    {
+        int gv[6];
+        gray6(y0 - 1, gv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            da[i] = gv[i + 2] - gv[i];
+            ha[i] = gv[i] + 2 * gv[i + 1] + gv[i + 2];
+        }
+        gray6(y0, gv);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            db[i] = gv[i + 2] - gv[i];
+            hb[i] = gv[i] + 2 * gv[i + 1] + gv[i + 2];
+        }
+    }
+    const bool full = x0 + 3 < p.W;
+#pragma unroll 2
+    for (int k = 0; k < ny; ++k) {
+        int gv[6];
+        gray6(y0 + k + 1, gv);
+        float m[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int dc = gv[i + 2] - gv[i], hc = gv[i] + 2 * gv[i + 1] + gv[i + 2];
+            const int gx = da[i] + 2 * db[i] + dc, gy = hc - ha[i];
+            m[i] = __fmul_rn(__fsqrt_rn((float)(gx * gx + gy * gy)), 0.125f);
+            da[i] = db[i];
+            ha[i] = hb[i];
+            db[i] = dc;
+            hb[i] = hc;
+        }
+        uint8_t *row = dst + (int64_t)(y0 + k) * p.dpitch;
+        if (F32) {
+            float *o = reinterpret_cast<float *>(row) + x0;
+            if (full && ((uintptr_t)o & 15) == 0) {
+                *reinterpret_cast<float4 *>(o) = make_float4(m[0], m[1], m[2], m[3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (x0 + i < p.W) o[i] = m[i];
+            }
+        } else {
+            uint8_t *o = row + x0;
+            uint8_t v[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) v[i] = (uint8_t)floorf(__fadd_rn(m[i], 0.5f));
+            if (full && ((uintptr_t)o & 3) == 0) {
+                *reinterpret_cast<uchar4 *>(o) = make_uchar4(v[0], v[1], v[2], v[3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (x0 + i < p.W) o[i] = v[i];
+            }
         }
     }
 }
@@ -92,7 +146,8 @@ cudaError_t launch_sobel(const SobelDesc &d, cudaStream_t stream)
     p.dst = d.dst;
     p.dpitch = d.dpitch;
     p.dbatch = d.dbatch;
-    const dim3 grid((d.W + kSW - 1) / kSW, (d.H + kSH - 1) / kSH, d.batch);
+    const int groups = (d.W + kGroup - 1) / kGroup;
+    const dim3 grid((groups + kThreads - 1) / kThreads, (d.H + kRun - 1) / kRun, d.batch);
     if (d.C == 3) {
         if (d.f32) sobel_kernel<3, true><<<grid, kThreads, 0, stream>>>(p);
         else sobel_kernel<3, false><<<grid, kThreads, 0, stream>>>(p);
