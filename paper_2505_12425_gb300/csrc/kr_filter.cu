@@ -52,15 +52,24 @@ __global__ void __launch_bounds__(kThreads) sobel_kernel(const __grid_constant__
     uint8_t *dst = p.dst + (int64_t)blockIdx.z * p.dbatch;
     // word reads stay inside the row: its bytes from 3 (x0 - 2) to 3 (x0 + 6) - 1
     const bool fast = C == 3 && x0 >= 2 && x0 + 5 <= p.W - 1;
+    // the fast path loads a row's words one row ahead of its use (load6, then gray6 of them)
+    auto load6 = [&](int y, uint32_t (&w)[6], int &sh) {
+        const uint8_t *a = src + (int64_t)min(max(y, 0), p.H - 1) * p.spitch + 3 * (x0 - 1);
+        sh = (int)((uintptr_t)a & 3);
+        const uint32_t *wp = reinterpret_cast<const uint32_t *>(a - sh);
+#pragma unroll
+        for (int t = 0; t < 6; ++t) w[t] = 4 * t < sh + 18 ? __ldg(wp + t) : 0u;
+    };
+    uint32_t wq[6];
+    int shq = 0;
     auto gray6 = [&](int y, int (&gv)[6]) {
         const uint8_t *row = src + (int64_t)min(max(y, 0), p.H - 1) * p.spitch;
         if (fast) {
-            const uint8_t *a = row + 3 * (x0 - 1);
-            const int sh = (int)((uintptr_t)a & 3);
-            const uint32_t *wp = reinterpret_cast<const uint32_t *>(a - sh);
             uint32_t w[6];
+            int sh = shq;
 #pragma unroll
-            for (int t = 0; t < 6; ++t) w[t] = 4 * t < sh + 18 ? __ldg(wp + t) : 0u;
+            for (int t = 0; t < 6; ++t) w[t] = wq[t];
+            load6(y + 1, wq, shq);   // the next row's words
             switch (sh) {
             case 0: gray6_words<0>(w, gv); break;
             case 1: gray6_words<1>(w, gv); break;
@@ -76,6 +85,7 @@ __global__ void __launch_bounds__(kThreads) sobel_kernel(const __grid_constant__
         }
     };
     int da[4], ha[4], db[4], hb[4];
+    if (fast) load6(y0 - 1, wq, shq);
     {
         int gv[6];
         gray6(y0 - 1, gv);
