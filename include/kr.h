@@ -75,7 +75,7 @@ typedef enum {
  *   dtype         KR_U8 or KR_F32 (f32 only as a destination);
  *   layout        KR_HWC: pixel (y, x) channel c at data + y*pitch + (x*C + c)*esize;
  *                 KR_CHW (f32 destinations only): at data + c*plane_stride + y*pitch + x*4;
- *   batch         number of images (>= 1); image n starts at data + n*batch_stride;
+ *   batch         number of images (1 .. 65535); image n starts at data + n*batch_stride;
  *   pitch         bytes between rows, >= width*C*esize (HWC) or width*4 (CHW);
  *   plane_stride  bytes between channel planes (CHW; ignored for HWC);
  *   batch_stride  bytes between images (ignored when batch == 1).

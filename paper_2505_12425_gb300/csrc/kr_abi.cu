@@ -49,7 +49,7 @@ static kr_status check_image(const kr_image_t *im, bool is_dst)
     if (im->channels != 1 && im->channels != 3) return KR_ERR_INVALID_ARG;
     if (im->dtype != KR_U8 && im->dtype != KR_F32) return KR_ERR_INVALID_ARG;
     if (im->layout != KR_HWC && im->layout != KR_CHW) return KR_ERR_INVALID_ARG;
-    if (im->batch < 1) return KR_ERR_INVALID_ARG;
+    if (im->batch < 1 || im->batch > kMaxSide) return KR_ERR_INVALID_ARG;   // batches index the grid's z
     const int es = esize_of(im->dtype);
     if (im->dtype == KR_F32) {
         if (((uintptr_t)im->data | (uintptr_t)im->pitch) & 3) return KR_ERR_INVALID_ARG;

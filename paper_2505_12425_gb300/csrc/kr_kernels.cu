@@ -401,10 +401,11 @@ cudaError_t launch_resample(const OpDesc &d, cudaStream_t stream)
 }
 
 // ---------------------------------------------------------------------------
-// Standalone RGB -> gray: one thread per 16-pixel chunk of a row. Rows whose
-// source and destination start on 16-byte boundaries move 48 bytes in through
-// three 128-bit loads and 16 bytes out through one 128-bit store; other rows
-// and the ragged tail go pixel by pixel.
+// Standalone RGB -> gray: one thread per 16-pixel chunk of a row (grid: chunks x
+// rows x images, no index divisions). Rows whose source and destination start on
+// 16-byte boundaries move 48 bytes in through three 128-bit loads and 16 bytes out
+// through one 128-bit store, each gray one dp2a on the pixel's word; other rows and
+// the ragged tail go pixel by pixel.
 // ---------------------------------------------------------------------------
 struct GrayParams {
     const uint8_t *src;
@@ -412,44 +413,38 @@ struct GrayParams {
     uint8_t *dst;
     int64_t dpitch, dbatch;
     int32_t H, W, chunks_x;
-    int64_t total;   // batch * H * chunks_x
 };
 
-__device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[12], int b)
+// (4899 R + 9617 G + 1868 B + 8192) >> 14 of the pixel in bytes 0..2 of P
+__device__ __forceinline__ uint32_t gray_of_word(uint32_t P)
 {
-    return (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+    return __dp2a_lo(4899u | (9617u << 16), P, 8192u + 1868u * ((P >> 16) & 255u)) >> 14;
 }
 
 __global__ void __launch_bounds__(kThreads) gray_kernel(const __grid_constant__ GrayParams p)
 {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < p.total; i += stride) {
-        const int64_t row = i / p.chunks_x;
-        const int cx = (int)(i - row * p.chunks_x);
-        const int64_t img = row / p.H;
-        const int y = (int)(row - img * p.H);
-        const uint8_t *s = p.src + img * p.sbatch + (int64_t)y * p.spitch + (int64_t)cx * 48;
-        uint8_t *d = p.dst + img * p.dbatch + (int64_t)y * p.dpitch + (int64_t)cx * 16;
-        const int n = min(16, p.W - cx * 16);
-        if (n == 16 && (((uintptr_t)s | (uintptr_t)d) & 15) == 0) {
-            uint32_t w[12];
-            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(s));
-            const uint4 b = __ldg(reinterpret_cast<const uint4 *>(s + 16));
-            const uint4 c = __ldg(reinterpret_cast<const uint4 *>(s + 32));
-            w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-            w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
-            w[8] = c.x; w[9] = c.y; w[10] = c.z; w[11] = c.w;
-            uint32_t o[4] = {0u, 0u, 0u, 0u};
+    const int cx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cx >= p.chunks_x) return;
+    const int y = blockIdx.y;
+    const uint8_t *s = p.src + (int64_t)blockIdx.z * p.sbatch + (int64_t)y * p.spitch + (int64_t)cx * 48;
+    uint8_t *d = p.dst + (int64_t)blockIdx.z * p.dbatch + (int64_t)y * p.dpitch + (int64_t)cx * 16;
+    const int n = min(16, p.W - cx * 16);
+    if (n == 16 && (((uintptr_t)s | (uintptr_t)d) & 15) == 0) {
+        const uint4 a = __ldg(reinterpret_cast<const uint4 *>(s));
+        const uint4 b = __ldg(reinterpret_cast<const uint4 *>(s + 16));
+        const uint4 c = __ldg(reinterpret_cast<const uint4 *>(s + 32));
+        const uint32_t w[13] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y, c.z, c.w, 0u};
+        uint32_t o[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const uint32_t g = gray_u8(byte_of(w, 3 * k), byte_of(w, 3 * k + 1), byte_of(w, 3 * k + 2));
-                o[k >> 2] |= g << (8 * (k & 3));
-            }
-            *reinterpret_cast<uint4 *>(d) = make_uint4(o[0], o[1], o[2], o[3]);
-        } else {
-            for (int k = 0; k < n; ++k)
-                d[k] = (uint8_t)gray_u8(__ldg(s + 3 * k), __ldg(s + 3 * k + 1), __ldg(s + 3 * k + 2));
+        for (int k = 0; k < 16; ++k) {
+            const int bo = 3 * k;   // pixel k: bytes bo .. bo+2
+            const uint32_t P = __funnelshift_r(w[bo >> 2], w[(bo >> 2) + 1], 8 * (bo & 3));
+            o[k >> 2] |= gray_of_word(P) << (8 * (k & 3));
         }
+        *reinterpret_cast<uint4 *>(d) = make_uint4(o[0], o[1], o[2], o[3]);
+    } else {
+        for (int k = 0; k < n; ++k)
+            d[k] = (uint8_t)gray_u8(__ldg(s + 3 * k), __ldg(s + 3 * k + 1), __ldg(s + 3 * k + 2));
     }
 }
 
@@ -475,13 +470,9 @@ cudaError_t launch_gray(const GrayDesc &d, cudaStream_t stream)
     p.H = d.H;
     p.W = d.W;
     p.chunks_x = (d.W + 15) / 16;
-    p.total = (int64_t)d.batch * d.H * p.chunks_x;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t want = (p.total + kThreads - 1) / kThreads;
-    const int blocks = (int)std::min<int64_t>(want, (int64_t)sms * 8);
-    gray_kernel<<<blocks, kThreads, 0, stream>>>(p);
+    const int bx = std::min(kThreads, 32 * ((p.chunks_x + 31) / 32));
+    const dim3 grid((p.chunks_x + bx - 1) / bx, d.H, d.batch);
+    gray_kernel<<<grid, bx, 0, stream>>>(p);
     return cudaGetLastError();
 }
 

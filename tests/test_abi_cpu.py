@@ -60,7 +60,7 @@ def _resize(lib, s, d, p=None):
 
 @pytest.mark.parametrize("bad", [
     dict(data=0), dict(h=0), dict(w=-1), dict(c=2), dict(c=4), dict(dtype=7), dict(pitch=14),
-    dict(batch=0), dict(h=70000)])
+    dict(batch=0), dict(batch=65536, bstride=60), dict(h=70000)])
 def test_resize_rejects_bad_source(lib, bad):
     s = _img(**bad)
     d = _img(data=0x900000, h=2, w=2)
