@@ -447,6 +447,8 @@ struct TileInfo {
                               // every coordinate lies in [0, 4094))
     int tma_ok;               // the TMA copy of the box completed
     int zero;                 // warp: the box misses the image, every sample is 0
+    int clamp;                // warp, replicated border: the box was clipped to the image and
+                              // every tap is clamped into it
 };
 
 template <int TW, int TH> struct TileShared {
@@ -687,7 +689,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         if (lane == 0) {
             // The box is NOT clipped to the image: staging fills its part outside the
             // image with zeros, which is the zero border, so every tap reads the box.
-            int fx0 = 0, fx1 = -1, fy0 = 0, fy1 = -1, fast = 0, zero = 0;
+            int fx0 = 0, fx1 = -1, fy0 = 0, fy1 = -1, fast = 0, zero = 0, clamp = 0;
             if (all_ok) {
                 fx0 = (int)floorf(mnx) - 1; fx1 = (int)floorf(mxx) + 3;
                 fy0 = (int)floorf(mny) - 1; fy1 = (int)floorf(mxy) + 3;
@@ -695,10 +697,18 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                 zero = !J.replicate && (fx1 < 0 || fx0 > J.W - 1 || fy1 < 0 || fy0 > J.H - 1);
                 // the one-fma weight form needs every coordinate in [0, 4094)
                 fast = J.allow_fast && mnx >= 1.f && mny >= 1.f && mxx < 4093.f && mxy < 4093.f;
+                if (J.replicate && (fx0 < 0 || fy0 < 0 || fx1 > J.W - 1 || fy1 > J.H - 1)) {
+                    // a tap clamped to the image lies in the box clipped to the image
+                    fx0 = min(max(fx0, 0), J.W - 1); fx1 = min(max(fx1, 0), J.W - 1);
+                    fy0 = min(max(fy0, 0), J.H - 1); fy1 = min(max(fy1, 0), J.H - 1);
+                    clamp = 1;
+                    fast = 0;
+                }
             }
             ti.fx0 = fx0; ti.fx1 = fx1; ti.fy0 = fy0; ti.fy1 = fy1;
             ti.fast = fast;
             ti.zero = zero;
+            ti.clamp = clamp;
         }
     }
     __syncthreads();
@@ -1058,6 +1068,42 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                 }
             };
             if (rawbox) fast3(IntC<TAPS_RAW>{}); else fast3(IntC<TAPS_WORDS>{});
+        } else if (OP != OP_RESIZE && CIN == 3 && staged && ti.clamp) {
+            // Replicated border, tile whose footprint crosses the image's edge: the box is the
+            // footprint clipped to the image; each tap is clamped into the image (its nearest
+            // edge pixel), which lies in the box, and read as one pixel word.
+            const int bx = J.W - 1 - fx0, by = J.H - 1 - fy0;   // box-relative image edges
+            auto px_at = [&](int yb, int xb) -> uint32_t {
+                if (rawbox) {
+                    const int off = yb * rstride + rph + 3 * xb;
+                    const uint32_t *wp = reinterpret_cast<const uint32_t *>(raw + (off & ~3));
+                    return __funnelshift_r(wp[0], wp[1], (uint32_t)off << 3);
+                }
+                return words[yb * sw + xb];
+            };
+            for (int r = r0 + warp; r < r1; r += kWarps) {
+                const ORow o = orow_of(r);
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) {
+                    const int c = lane + 32 * j;
+                    if (c < nx) {
+                        float sx, sy;
+                        map_coord<OP>(J.M, tx0 + c, ty0 + r, sx, sy);   // valid: the tile's corners are
+                        int x0, y0, qx, qy;
+                        warp_weight(sx, x0, qx);
+                        warp_weight(sy, y0, qy);
+                        float fx = 0.f, fy = 0.f;
+                        if (OT::is_f32) {
+                            fx = __fsub_rn(sx, floorf(sx));
+                            fy = __fsub_rn(sy, floorf(sy));
+                        }
+                        const int xa = min(max(x0 - fx0, -fx0), bx), xb = min(max(x0 + 1 - fx0, -fx0), bx);
+                        const int ya = min(max(y0 - fy0, -fy0), by), yb = min(max(y0 + 1 - fy0, -fy0), by);
+                        emit<CIN, OUTK>(J, o, c, px_at(ya, xa), px_at(ya, xb), px_at(yb, xa), px_at(yb, xb), qx, qy,
+                                        fx, fy);
+                    }
+                }
+            }
         } else if (OP != OP_RESIZE && CIN == 3 && staged) {
             // Medium path (warp tiles with coordinates outside [0, 4094)): the exact weight
             // formula per pixel; every tap still lies in the zero-filled box.
