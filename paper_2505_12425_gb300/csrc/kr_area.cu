@@ -1,4 +1,5 @@
-// Area (antialiased) downscale: each output pixel is the overlap-weighted mean of the
+// Area (antialiased) downscale, a variant of the paper's downsizing (Sec. III), which
+// prints no interpolation rule: each output pixel is the overlap-weighted mean of the
 // source over its footprint [x W/w, (x+1) W/w) x [y H/h, (y+1) H/h). In units of 1/w and
 // 1/h of a pixel the overlaps are integers, so the weighted sum S is exact (32-bit when
 // 255 W H < 2^32, else 64-bit) and u8 = floor((2 S + W H) / (2 W H)); f32 outputs take

@@ -1,22 +1,25 @@
-// Device-side tile engine of the resampling kernels (sm_103a).
+// Device-side tile engine of the resampling kernels (sm_103a): bilinear resize and the
+// affine and perspective warps of Sec. III / Sec. II-A, with the fused gray and u8 -> f32
+// normalisation epilogues of Sec. III.
 //
 // One CTA of kThreads threads produces one TW x TH tile of output pixels:
-//   1. plan: the source box of the tile (the bounding box of every tap, from
-//      the resize axis tables or from the warp map at the tile corners) and a
-//      per-tile "fast" flag;
-//   2. stage: the box's source rows are copied into shared memory as whole
-//      16-byte chunks with cp.async; 3-channel rows are then re-laid out as one
-//      32-bit word per pixel (R, G, B, pad) so that every tap is one aligned
-//      32-bit shared load;
-//   3. compute: fast tiles (every tap inside the box, coordinates in the range
-//      where the cheap weight form is exact) run a branch-free pixel loop; other
-//      tiles (image border, huge or non-finite coordinates, boxes too large for
-//      shared memory) take the general per-pixel path, which reads taps from
-//      the box when they are inside it and from global memory (zero outside the
-//      image) otherwise;
-//   4. write-out: results go into a shared copy of the output tile whose rows
-//      keep the 16-byte phase of their global rows, then leave through 128-bit
-//      coalesced stores (head and tail bytes one per lane).
+//   1. plan: the source box of the tile (the bounding box of every tap, from the resize
+//      axis tables or from the warp map at the tile corners) and a per-tile "fast" flag;
+//   2. stage: the box's source rows are copied into shared memory by one 3-D TMA copy (a
+//      {word, row, image} tensor map; the part of a warp box outside the image arrives as
+//      zeros, the zero border), else by one bulk copy per row, else as 16-byte cp.async
+//      chunks; the copies complete on an mbarrier with a bounded wait. TMA- and bulk-staged
+//      rows share one 16-byte phase, so 3-channel tap pairs are read straight from them
+//      ("raw taps"); cp.async-staged 3-channel rows are re-laid as one word per pixel. With
+//      the replicated border a box crossing the image's edge is clipped to the image and
+//      its taps are clamped into it;
+//   3. compute: fast tiles (every tap inside the box, coordinates in the range where the
+//      packed one-fma weight forms are exact) run a branch-free pixel loop; other tiles
+//      (coordinates outside that range, boxes too large for shared memory, non-finite or
+//      huge coordinates) take the medium or general per-pixel paths;
+//   4. write-out: results go into a shared copy of the output tile (two bands of rows for
+//      f32) and leave through a TMA store per band, else through 128-bit coalesced stores
+//      (head and tail bytes one per lane).
 //
 // Arithmetic (definitions shared with the C ABI documentation):
 //   resize   sx = (x + 1/2) W / w - 1/2 as the exact rational num/den, clamp to

@@ -1,5 +1,6 @@
-// Sobel 3x3 gradient magnitude (u8 HWC source, 1 or 3 channels; 3 channels are first the
-// u8 BT.601 gray), replicated border, f32 or u8 single-channel output:
+// Sobel 3x3 gradient magnitude (the filter of the Sec. V example; u8 HWC source, 1 or 3
+// channels; 3 channels are first the u8 BT.601 gray), replicated border, f32 or u8
+// single-channel output:
 //   m = sqrt(gx^2 + gy^2) / 8 (normalised kernels), u8 = floor(m + 1/2).
 // A thread owns 4 output columns x0 .. x0+3 of a run of 16 output rows and walks down the
 // run: per source row it forms the gray values of the 6 source pixels x0-1 .. x0+4, their

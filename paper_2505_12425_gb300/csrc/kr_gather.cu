@@ -1,6 +1,6 @@
-// Pixel gathers: nearest-neighbour resize and horizontal flip (u8, 1 or 3
-// channels, HWC, any pitch, batched). Each output pixel copies one source pixel,
-// so the kernels move bytes only.
+// Pixel gathers: nearest-neighbour resize (Sec. IV-A) and horizontal flip (Sec. III,
+// Sec. IV-A) of u8 images (1 or 3 channels, HWC, any pitch, batched). Each output pixel
+// copies one source pixel, so the kernels move bytes only.
 //
 //   nearest  output (x, y) <- source (((2x + 1) W) div (2w), ((2y + 1) H) div (2h))
 //            (half-pixel centres: the source pixel covering the output centre)
