@@ -180,9 +180,10 @@ kr_status kr_flip_horizontal(const kr_image_t *src, const kr_image_t *dst, kr_st
  * source pixel weighted by its overlap area (exact integer weights); u8 dst:
  * that mean rounded half up; f32 dst: mean / 255, then the fused normalise.
  * src: u8 HWC C = 1 or 3. dst: same channels and batch (no KR_GRAY),
- * w <= W and h <= H (else KR_ERR_INVALID_ARG). KR_ERR_UNSUPPORTED when the
- * footprint of 64 output columns exceeds 96 KB of shared memory (a reduction
- * of several hundred times along both axes at once).
+ * w <= W and h <= H (else KR_ERR_INVALID_ARG). KR_ERR_UNSUPPORTED when two
+ * source rows of one output column's footprint exceed 96 KB of shared memory
+ * (more than about 16000 source columns per output column with 3 channels,
+ * 49000 with 1), reported before anything is enqueued.
  */
 kr_status kr_resize_area(const kr_image_t *src, const kr_image_t *dst, const kr_post_t *post, kr_stream_t stream);
 
