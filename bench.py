@@ -275,7 +275,8 @@ def serving_compare(torch, kr, dev, rates=(2000, 5000, 10000, 20000, 40000, 8000
                     seconds=1.0):
     """Poisson request streams (sizes log-uniform 320..3840 x 240..2160, op uniform over
     resize / warp / gray) over a device-resident pool of 64 pitched images, 8 GB in-flight budget:
-    continuous batching (policy 0) vs one launch per request (policy 1)."""
+    continuous batching (policy 0) vs one launch per request (policy 1) vs size-aware continuous
+    batching (policy 2: requests of at least 2^20 output pixels launch alone)."""
     sizes = inputs.pool_sizes(1004, 64)
     pool = [pitched(torch, inputs.uniform_image(5000 + i, H, W, 3), dev) for i, (H, W) in enumerate(sizes)]
     arena = torch.empty(8 << 30, dtype=torch.uint8, device=dev)
@@ -286,19 +287,19 @@ def serving_compare(torch, kr, dev, rates=(2000, 5000, 10000, 20000, 40000, 8000
         dur = seconds if rate <= 80000 else seconds * 80000 / rate * 2
         reqs = inputs.request_stream(1004, float(rate), dur, pool=64)
         px = sum(r.h * r.w for r in reqs)
-        for policy in (0, 1):
+        for policy in (0, 1, 2):
             res = kr.kr_serve_run(reqs, pool, arena, budget_bytes=8 << 30, max_batch=64, streams=4, policy=policy)
             lat = np.array([res[i].t_done - r.t_arrival for i, r in enumerate(reqs)]) * 1e3
             t_end = max(res[i].t_done for i in range(len(reqs)))
             nb = len({round(res[i].t_launch, 9) for i in range(len(reqs))})
             out["runs"].append({
-                "rate": rate, "policy": "batched" if policy == 0 else "per_image", "requests": len(reqs),
+                "rate": rate, "policy": ("batched", "per_image", "size_aware")[policy], "requests": len(reqs),
                 "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
                 "p999_ms": round(float(np.percentile(lat, 99.9)), 3),
                 "gpx_s": round(px / t_end / 1e9, 3), "launches": nb, "mean_batch": round(len(reqs) / nb, 2)})
     best = {}
     for slo in (2.0, 5.0, 10.0):
-        for pol in ("batched", "per_image"):
+        for pol in ("batched", "per_image", "size_aware"):
             ok = [r for r in out["runs"] if r["policy"] == pol and r["p99_ms"] <= slo]
             best[f"{pol}_gpx_s_at_p99<={slo:g}ms"] = max((r["gpx_s"] for r in ok), default=None)
     out["best"] = best

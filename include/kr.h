@@ -325,12 +325,17 @@ typedef struct {
  * limit); max_batch: items per ragged launch; streams: launches in flight (the
  * library creates and destroys these streams and their events); policy: 0 =
  * continuous batching (kr_batch_submit on a free slot with every admitted
- * request), 1 = one launch per request; workspaces / ws_bytes_each: policy 0
+ * request), 1 = one launch per request, 2 = size-aware continuous batching (on
+ * a free slot, every admitted request of at least direct_px output pixels is
+ * launched alone and the others go into one kr_batch_submit, all on the slot's
+ * stream: large images fill the GPU by themselves, small ones share a launch);
+ * workspaces / ws_bytes_each: policies 0 and 2
  * only, `streams` device workspaces of ws_bytes_each >=
  * kr_batch_workspace_size(max_batch) bytes, caller-owned; retain_outputs: 0 =
  * a request's arena space is reused once it completes (the client is taken to
  * consume each output at its completion), 1 = every output keeps its space until
- * the run ends (the arena must then hold all outputs, else KR_ERR_NO_SPACE).
+ * the run ends (the arena must then hold all outputs, else KR_ERR_NO_SPACE);
+ * direct_px: policy 2's threshold (0 = 2^20 output pixels).
  */
 typedef struct {
     const kr_image_t *pool;
@@ -344,6 +349,7 @@ typedef struct {
     void *workspaces;
     size_t ws_bytes_each;
     int32_t retain_outputs;
+    int64_t direct_px;
 } kr_serve_config_t;
 
 /* Per request: admission, launch and observed completion times (seconds from the

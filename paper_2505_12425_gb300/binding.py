@@ -68,7 +68,7 @@ class KrServeConfig(ctypes.Structure):
                 ("out_arena_bytes", ctypes.c_size_t), ("hbm_budget_bytes", ctypes.c_size_t),
                 ("max_batch", ctypes.c_int32), ("streams", ctypes.c_int32), ("policy", ctypes.c_int32),
                 ("workspaces", ctypes.c_void_p), ("ws_bytes_each", ctypes.c_size_t),
-                ("retain_outputs", ctypes.c_int32)]
+                ("retain_outputs", ctypes.c_int32), ("direct_px", ctypes.c_int64)]
 
 
 class KrServeResult(ctypes.Structure):
@@ -381,7 +381,7 @@ def requests_array(reqs) -> ctypes.Array:
 
 
 def kr_serve_run(reqs, pool, arena: torch.Tensor, budget_bytes: int = 8 << 30, max_batch: int = 64,
-                 streams: int = 4, policy: int = 0, retain_outputs: bool = False):
+                 streams: int = 4, policy: int = 0, retain_outputs: bool = False, direct_px: int = 0):
     """Serve `reqs` (see inputs.request_stream) over the device image `pool` (list of u8 HWC
     tensors); outputs are carved from the device tensor `arena`. Returns the kr_serve_result_t
     array (seconds from the start of the run; byte offsets into the arena)."""
@@ -392,14 +392,14 @@ def kr_serve_run(reqs, pool, arena: torch.Tensor, budget_bytes: int = 8 << 30, m
         imgs[i] = image(t)
     ws = None
     ws_each = 0
-    if policy == 0:
+    if policy in (0, 2):
         ws_each = kr_batch_workspace_size(max_batch)
         ws_each = (ws_each + 255) // 256 * 256
         ws = torch.empty(ws_each * streams, dtype=torch.uint8, device=arena.device)
     cfg = KrServeConfig(imgs, len(pool), ctypes.c_void_p(arena.data_ptr()), arena.numel() * arena.element_size(),
                         budget_bytes, max_batch, streams, policy,
                         ctypes.c_void_p(ws.data_ptr() if ws is not None else 0), ws_each,
-                        1 if retain_outputs else 0)
+                        1 if retain_outputs else 0, direct_px)
     res = (KrServeResult * len(arr))()
     torch.cuda.synchronize()
     _check(lib.kr_serve_run(arr, len(arr), ctypes.byref(cfg), res), "kr_serve_run")

@@ -14,6 +14,9 @@
 //             streams overlap on the device;
 //             (policy 1) every admitted request is launched alone, round-robin over
 //             the K streams (the per-image baseline);
+//             (policy 2) as policy 0, but on the free slot's stream every admitted
+//             request of at least direct_px output pixels is launched alone and
+//             only the smaller ones share the ragged launch;
 //   completion an event per launch is polled; its requests get their completion
 //             time, their bytes leave the budget and their arena space is freed.
 // The caller reads outputs from the arena at the offsets reported per request.
@@ -89,9 +92,9 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
 {
     if (n < 0 || (n > 0 && (!reqs || !results)) || !cfg) return KR_ERR_INVALID_ARG;
     if (!cfg->pool || cfg->pool_n < 1 || !cfg->out_arena || cfg->streams < 1 || cfg->streams > 64 ||
-        cfg->max_batch < 1 || (cfg->policy != 0 && cfg->policy != 1))
+        cfg->max_batch < 1 || cfg->policy < 0 || cfg->policy > 2 || cfg->direct_px < 0)
         return KR_ERR_INVALID_ARG;
-    if (cfg->policy == 0 && (!cfg->workspaces || cfg->ws_bytes_each < kr_batch_workspace_size(cfg->max_batch)))
+    if (cfg->policy != 1 && (!cfg->workspaces || cfg->ws_bytes_each < kr_batch_workspace_size(cfg->max_batch)))
         return KR_ERR_NO_SPACE;
     for (int i = 0; i < cfg->pool_n; ++i) {
         const kr_image_t &p = cfg->pool[i];
@@ -124,7 +127,7 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
     kr_status status = KR_OK;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking);
-    const int n_events = cfg->policy == 0 ? K : std::min(4096, std::max(K, n));
+    const int n_events = cfg->policy != 1 ? K : std::min(4096, std::max(K, n));
     for (int k = 0; k < n_events && e == cudaSuccess; ++k) {
         cudaEvent_t ev;
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -148,6 +151,12 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
         results[i].status = KR_OK;
     }
 
+    // one request through its single-image call
+    auto launch_alone = [&](const kr_work_t &w, cudaStream_t s) -> kr_status {
+        if (w.op == KR_OP_RESIZE) return kr_resize_bilinear(&w.src, &w.dst, nullptr, (kr_stream_t)s);
+        if (w.op == KR_OP_WARP) return kr_warp_affine(&w.src, &w.dst, w.M, nullptr, (kr_stream_t)s);
+        return kr_rgb_to_gray(&w.src, &w.dst, (kr_stream_t)s);
+    };
     auto make_work = [&](int i, kr_work_t &w) {
         const kr_request_t &r = reqs[i];
         std::memset(&w, 0, sizeof(w));
@@ -207,24 +216,33 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
             break;
         }
         // launches
-        if (cfg->policy == 0) {
+        if (cfg->policy != 1) {
+            const int64_t direct_px = cfg->direct_px > 0 ? cfg->direct_px : (int64_t)1 << 20;
             for (int k = 0; k < K && !admitted.empty(); ++k) {
                 if (slot_busy[k]) continue;
                 Launch L;
                 L.slot = k;
                 work.clear();
+                const double tl = now_s();
+                kr_status st = KR_OK;
                 while (!admitted.empty() && (int)L.reqs.size() < cfg->max_batch) {
                     const int i = admitted.front();
                     admitted.pop_front();
                     kr_work_t w;
                     make_work(i, w);
-                    work.push_back(w);
                     L.reqs.push_back(i);
+                    if (cfg->policy == 2 && (int64_t)w.dst.width * w.dst.height >= direct_px) {
+                        st = launch_alone(w, streams[k]);
+                        if (st != KR_OK) break;
+                    } else {
+                        work.push_back(w);
+                    }
                 }
-                void *ws = (uint8_t *)cfg->workspaces + (size_t)k * cfg->ws_bytes_each;
-                const double tl = now_s();
-                kr_status st = kr_batch_submit(work.data(), (int32_t)work.size(), ws, cfg->ws_bytes_each, nullptr,
-                                               (kr_stream_t)streams[k]);
+                if (st == KR_OK && !work.empty()) {
+                    void *ws = (uint8_t *)cfg->workspaces + (size_t)k * cfg->ws_bytes_each;
+                    st = kr_batch_submit(work.data(), (int32_t)work.size(), ws, cfg->ws_bytes_each, nullptr,
+                                         (kr_stream_t)streams[k]);
+                }
                 if (st != KR_OK) { status = st; break; }
                 L.done = event_pool.back();
                 event_pool.pop_back();
@@ -243,10 +261,7 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
                 cudaStream_t s = streams[rr];
                 rr = (rr + 1) % K;
                 const double tl = now_s();
-                kr_status st;
-                if (w.op == KR_OP_RESIZE) st = kr_resize_bilinear(&w.src, &w.dst, nullptr, (kr_stream_t)s);
-                else if (w.op == KR_OP_WARP) st = kr_warp_affine(&w.src, &w.dst, w.M, nullptr, (kr_stream_t)s);
-                else st = kr_rgb_to_gray(&w.src, &w.dst, (kr_stream_t)s);
+                const kr_status st = launch_alone(w, s);
                 if (st != KR_OK) { status = st; break; }
                 Launch L;
                 L.reqs.push_back(i);

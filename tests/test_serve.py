@@ -59,6 +59,11 @@ def test_serve_rejects_bad_configs(lib):
     reqs = (kr.KrRequest * 1)(_req())
     cfg.policy = 0                                             # batching needs workspaces
     assert lib.kr_serve_run(reqs, 1, ctypes.byref(cfg), res) == 5
+    cfg.policy = 2                                             # so does size-aware batching
+    assert lib.kr_serve_run(reqs, 1, ctypes.byref(cfg), res) == 5
+    cfg.policy, cfg.direct_px = 1, -1                          # negative threshold
+    assert lib.kr_serve_run(reqs, 1, ctypes.byref(cfg), res) == 1
+    cfg.direct_px = 0
     cfg.policy = 3
     assert lib.kr_serve_run(reqs, 1, ctypes.byref(cfg), res) == 1
     cfg.policy, cfg.streams = 1, 0
@@ -116,15 +121,19 @@ def _from_arena(arena, res, r):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("policy", [0, 1])
+@pytest.mark.parametrize("policy", [0, 1, 2])
 def test_served_results_equal_results_alone(lib, policy):
     dev = torch.device("cuda:0")
     pool = _pool(dev)
     reqs = _stream(pool, rate=4000.0, duration=0.08, seed=5 + policy)
     assert len(reqs) > 100
     arena = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+    # policy 2 with a low threshold: some requests launch alone, the rest share ragged launches
     res = kr.kr_serve_run(reqs, pool, arena, budget_bytes=1 << 30, max_batch=32, streams=4, policy=policy,
-                          retain_outputs=True)
+                          retain_outputs=True, direct_px=20000 if policy == 2 else 0)
+    if policy == 2:
+        big = sum(1 for r in reqs if r.h * r.w >= 20000)
+        assert 0 < big < len(reqs)
     for i, r in enumerate(reqs):
         assert res[i].t_done >= res[i].t_launch >= res[i].t_admit >= r.t_arrival - 1e-3
         got = _from_arena(arena, res[i], r)
