@@ -40,7 +40,7 @@ struct AreaParams {
     int32_t segrow;                 // bytes per staged row (a multiple of 16)
     int32_t K;                      // source rows per ring slot
     int32_t nbuf;                   // ring slots (2 .. 4)
-    int32_t fin32;                  // 2 S + W H < 2^32: the u8 estimate converts a 32-bit value
+    int32_t fin32;                  // 512 W H < 2^32: the u8 rounding runs in 32-bit integers
     float inv_wh;                   // 1 / (W H)
     float inv_2wh;                  // 1 / (2 W H)
     float scale[3], bias[3];
@@ -250,10 +250,12 @@ __global__ void __launch_bounds__(kThreads, 4) area_kernel(const __grid_constant
                             // one of the quotient; one step each way makes it exact
                             unsigned qv;
                             if (!WIDE && p.fin32) {
+                                // 512 W H < 2^32: every product below fits 32 bits
                                 const unsigned num = 2u * (unsigned)cur[k] + (unsigned)wh, den = 2u * (unsigned)wh;
                                 qv = (unsigned)__fmul_rz(__uint2float_rn(num), p.inv_2wh);
-                                if ((u64)qv * den > num) --qv;
-                                else if ((u64)(qv + 1) * den <= num) ++qv;
+                                const unsigned t = qv * den;
+                                if (t > num) --qv;
+                                else if (t + den <= num) ++qv;
                             } else {
                                 const u64 num = 2ull * (u64)cur[k] + wh, den = 2ull * wh;
                                 qv = (unsigned)__fmul_rz((float)num, p.inv_2wh);
@@ -332,7 +334,7 @@ cudaError_t launch_area(const AreaDesc &d, cudaStream_t stream, bool &too_large)
     p.R = (int)std::max(1LL, std::min(32LL, strips * d.h * d.batch / (8LL * std::max(1, sms))));
     const size_t smem = (size_t)nbuf * (size_t)(K * segrow);
     const bool wide = 255.0 * (double)d.W * (double)d.H >= 4294967296.0;
-    p.fin32 = 511.0 * (double)d.W * (double)d.H < 4294967296.0;
+    p.fin32 = 512.0 * (double)d.W * (double)d.H < 4294967296.0;
     const void *k = d.C == 3 ? (wide ? (const void *)area_kernel<true, 3> : (const void *)area_kernel<false, 3>)
                              : (wide ? (const void *)area_kernel<true, 1> : (const void *)area_kernel<false, 1>);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAreaSmemCap);
