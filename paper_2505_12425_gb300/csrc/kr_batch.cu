@@ -622,8 +622,7 @@ static kr_status enqueue(const Packed &P, void *ws, int cfg, int ctas_per_sm, bo
             void *args[] = {&ws};
             for (int k = 0; k < kGroups && e == cudaSuccess; ++k) {
                 if (!L.grid[k]) continue;
-                cudaKernelNodeParams kp;
-                std::memset(&kp, 0, sizeof(kp));
+                cudaKernelNodeParams kp{};
                 kp.func = (void *)g_cfgs[cfg].kernels[k];
                 kp.gridDim = dim3(L.grid[k]);
                 kp.blockDim = dim3(kThreads);
