@@ -25,7 +25,7 @@
 #include <string>
 #include <vector>
 
-#include "kr_device.cuh"
+#include "kr_tile.cuh"
 #include "kr_internal.h"
 
 namespace kr {

@@ -8,7 +8,7 @@
 
 #include <cudaTypedefs.h>
 
-#include "kr_device.cuh"
+#include "kr_tile.cuh"
 #include "kr_internal.h"
 
 namespace kr {
@@ -19,6 +19,7 @@ constexpr int kTH = 32;
 
 // Device error flags of the per-operation kernels (bit 0: a bounded TMA wait ran out).
 static __device__ unsigned g_kr_device_err;
+
 
 // Largest raw box (bytes of 16-byte chunk rows) a 3-channel launch stages.
 constexpr long long kRawBoxCap = 56 * 1024;
@@ -47,8 +48,15 @@ struct OpParams {
 
 // ROWS: instantiated for launches whose 3-channel boxes are staged by bulk row copies (no
 // tensor map, 16-byte aligned rows); the others do without that code.
+// CTAs per SM the register allocation leaves room for: u8 kinds 8 (32 registers), f32 kinds
+// 6 (40).
+template <int OP, int OUTK> constexpr int resample_min_ctas()
+{
+    return (OUTK == OUT_F32 || OUTK == OUT_F32_GRAY) ? 6 : 8;
+}
+
 template <int OP, int CIN, int OUTK, int TW, int TH, bool ROWS>
-__global__ void __launch_bounds__(kThreads) resample_kernel(const __grid_constant__ OpParams p)
+__global__ void __launch_bounds__(kThreads, resample_min_ctas<OP, OUTK>()) resample_kernel(const __grid_constant__ OpParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ TileShared<TW, TH> ts;
@@ -251,6 +259,7 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
     constexpr int TW = kTW, TH = kTH;
     auto kern_map = resample_kernel<OP, CIN, OUTK, TW, TH, false>;
     auto kern_rows = resample_kernel<OP, CIN, OUTK, TW, TH, CIN == 3>;
+    constexpr int ob = out_stage_bytes<OUTK, CIN, TW, TH>();
     static unsigned attr_done = 0;   // one bit per device ordinal (< 32)
     int dev = 0;
     cudaGetDevice(&dev);
@@ -286,7 +295,6 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
     constexpr int nm = OP == OP_PERSP ? 9 : 6;   // floats per image map
     for (int b0 = 0; b0 < d.batch; b0 += per_launch) {
         const int nb = std::min(per_launch, d.batch - b0);
-        constexpr int ob = out_stage_bytes<OUTK, CIN, TW, TH>();
         Budget bud;
         std::memset(p.fast_mask, 0, sizeof(p.fast_mask));
         // Raw-tap box bound (3 channels): the largest tile box of the launch whose raw rows
