@@ -27,6 +27,7 @@
 
 #include "kr_tile.cuh"
 #include "kr_internal.h"
+#include "kr_pipe.cuh"
 
 namespace kr {
 
@@ -74,7 +75,8 @@ struct alignas(16) WsHeader {
     int items[16];
     int first_tile[16];       // group g: tiles [first_tile[g], first_tile[g] + tiles[g])
     int tiles[16];
-    int pad1[44];
+    int stage_bytes[16];      // group g, pipelined kernel: bytes of one staging slot
+    int pad1[28];
 };
 static_assert(sizeof(WsHeader) == 512, "header is 512 bytes");
 // item flags: the warp map allows the fast path; region A is sized for raw boxes; the
@@ -83,6 +85,17 @@ constexpr int ITEM_FAST = 1, ITEM_RAW = 2, ITEM_ROWS16 = 4, ITEM_REPLICATE = 8;
 
 // Device error flags of the ragged kernel (bit 0: a bounded staging wait ran out).
 static __device__ unsigned g_kr_batch_err;
+
+// Bound of the first wait for a tile's staged box in the pipelined ragged kernels (0: give
+// up at once); the second wait, for copies still in flight, always has the full bound.
+static __device__ unsigned long long g_kr_stage_wait_ns = kTmaWaitNs;
+
+// Staging ring depth and tile shape of the pipelined ragged kernels.
+constexpr int kPipeStages = 2;
+constexpr int kPipeTW = 64, kPipeTH = 32;
+
+// Kinds that run on the pipelined engine (3-channel resize and warp).
+constexpr bool pipe_kind(int kind) { return kind != KIND_GRAY && ((kind >> 4) & 15) == 3; }
 
 static constexpr size_t prefix_bytes(int n) { return ((size_t)(n + 1) * 4 + 15) & ~(size_t)15; }
 static constexpr size_t worklist_bytes(int n)
@@ -183,6 +196,93 @@ __global__ void __launch_bounds__(kThreads, kind_is_f32(kKinds[G]) ? 4 : 5) ragg
     }
 }
 
+// Tiles of one kind group of a ragged work list for the pipelined kernels: the producer
+// claims kClaim consecutive tiles at a time from the group's counter in the work-list header
+// (so CTAs that drew cheap tiles take more), and since a CTA's tile indices only grow, the
+// owning item is found by a forward scan of the tile prefix from the previous tile's item,
+// 32 entries per warp-wide read.
+struct RaggedPipeTiles {
+    static constexpr bool kSameGeometry = false;
+    static constexpr int kClaim = 2;
+    unsigned *next;   // the group's tile counter
+    const WorkItem *items;
+    const int *prefix;
+    int t0, tiles, last_item;
+    int cur;          // item of the previous tile (first item of the group at the start)
+    int claim = 0, left = 0;   // next tile of the current claim, tiles left in it
+    __device__ bool tile(int, int lane, int &job, int &tx, int &ty)
+    {
+        if (left == 0) {
+            int c = 0;
+            if (lane == 0) c = (int)atomicAdd(next, (unsigned)kClaim);
+            claim = __shfl_sync(0xffffffffu, c, 0);
+            left = kClaim;
+        }
+        const int tl = claim++;
+        --left;
+        if (tl >= tiles) return false;
+        const int t = t0 + tl;
+        for (;;) {
+            const int idx = cur + 1 + lane;
+            const bool le = idx <= last_item && __ldg(prefix + idx) <= t;
+            const unsigned m = __ballot_sync(0xffffffffu, le);   // the prefix grows: a run of lanes
+            cur += __popc(m);
+            if (m != 0xffffffffu) break;
+        }
+        job = cur;
+        const int local = t - __ldg(prefix + cur);
+        const int txs = __ldg(&items[cur].tiles_x);
+        ty = local / txs;
+        tx = local - ty * txs;
+        return true;
+    }
+    __device__ void job(int j, Job &J) const { J = job_of(items[j]); }
+    __device__ unsigned *err() const { return &g_kr_batch_err; }
+    __device__ uint64_t first_wait_ns() const { return g_kr_stage_wait_ns; }
+};
+
+// Pipelined ragged kernel of kind group G (a 3-channel resize or warp kind): persistent CTAs
+// of one producer warp and kPipeConsumers blending threads over the group's tiles.
+template <int G>
+__global__ void __launch_bounds__(kPipeThreads, 3) ragged_pipe_kernel(uint8_t *ws)
+{
+    // The next kind's kernel in the stream may start now: the kinds share no data.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    constexpr int KIND = kKinds[G];
+    constexpr int OP = KIND & 15, OUTK = (KIND >> 8) & 15;
+    static_assert(pipe_kind(KIND), "3-channel resample kinds only");
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ PipeShared<kPipeTW, kPipeTH, kPipeStages> sh;
+    const WsHeader *hdr = reinterpret_cast<const WsHeader *>(ws);
+    const WorkItem *items = reinterpret_cast<const WorkItem *>(ws + sizeof(WsHeader));
+    RaggedPipeTiles P;
+    P.next = &reinterpret_cast<WsHeader *>(ws)->next[G];
+    P.items = items;
+    P.prefix = reinterpret_cast<const int *>(items + hdr->n);
+    P.t0 = hdr->first_tile[G];
+    P.tiles = hdr->tiles[G];
+    P.cur = hdr->first_item[G];
+    P.last_item = hdr->first_item[G] + hdr->items[G] - 1;
+    pipe_run<OP, OUTK, kPipeTW, kPipeTH, kPipeStages>(P, sh, smem, hdr->stage_bytes[G],
+                                                        pipe_unit_bytes<OUTK, kPipeTW>());
+}
+
+// Dynamic shared bytes of a pipelined ragged launch with staging slots of `stage` bytes.
+static size_t pipe_smem(int kind, int stage)
+{
+    const int outk = (kind >> 8) & 15;
+    const int unit = outk == OUT_U8 ? pipe_unit_bytes<OUT_U8, kPipeTW>()
+                     : outk == OUT_U8_GRAY ? pipe_unit_bytes<OUT_U8_GRAY, kPipeTW>()
+                     : outk == OUT_F32 ? pipe_unit_bytes<OUT_F32, kPipeTW>()
+                                       : pipe_unit_bytes<OUT_F32_GRAY, kPipeTW>();
+    return (size_t)kPipeStages * stage + (size_t)2 * (kPipeConsumers / 32) * unit;
+}
+
+cudaError_t set_stage_wait_ns_batch(unsigned long long ns)
+{
+    return cudaMemcpyToSymbol(g_kr_stage_wait_ns, &ns, sizeof(ns));
+}
+
 cudaError_t batch_error_flags(unsigned *flags, bool clear)
 {
     cudaError_t e = cudaMemcpyFromSymbol(flags, g_kr_batch_err, sizeof(unsigned));
@@ -215,14 +315,26 @@ template <int TW, int TH> static constexpr int max_region_b()
      (const void *)ragged_kernel<TW, TH, 8>, (const void *)ragged_kernel<TW, TH, 9>,                            \
      (const void *)ragged_kernel<TW, TH, 10>, (const void *)ragged_kernel<TW, TH, 11>,                          \
      (const void *)ragged_kernel<TW, TH, 12>}
+// Configuration 0 (64 x 32 tiles) runs the 3-channel resample kinds on the pipelined kernel.
 static TileCfg g_cfgs[] = {
-    {64, 32, KR_KERNELS(64, 32), kFootCap + max_region_b<64, 32>()},
+    {64, 32,
+     {(const void *)ragged_pipe_kernel<0>, (const void *)ragged_pipe_kernel<1>, (const void *)ragged_pipe_kernel<2>,
+      (const void *)ragged_pipe_kernel<3>, (const void *)ragged_kernel<64, 32, 4>,
+      (const void *)ragged_kernel<64, 32, 5>, (const void *)ragged_pipe_kernel<6>,
+      (const void *)ragged_pipe_kernel<7>, (const void *)ragged_pipe_kernel<8>, (const void *)ragged_pipe_kernel<9>,
+      (const void *)ragged_kernel<64, 32, 10>, (const void *)ragged_kernel<64, 32, 11>,
+      (const void *)ragged_kernel<64, 32, 12>},
+     kFootCap + max_region_b<64, 32>()},
     {32, 32, KR_KERNELS(32, 32), kFootCap + max_region_b<32, 32>()},
     {128, 16, KR_KERNELS(128, 16), kFootCap + max_region_b<128, 16>()},
     {64, 16, KR_KERNELS(64, 16), kFootCap + max_region_b<64, 16>()},
 };
 #undef KR_KERNELS
 constexpr int kNumCfgs = sizeof(g_cfgs) / sizeof(g_cfgs[0]);
+
+// Group g of configuration cfg runs on the pipelined kernel.
+static bool uses_pipe(int cfg, int g) { return cfg == 0 && pipe_kind(kKinds[g]); }
+static int threads_of(int cfg, int g) { return uses_pipe(cfg, g) ? kPipeThreads : kThreads; }
 
 // The output stage of process_tile (out_stage_bytes) for a runtime kind: f32 tiles stage
 // one band of th / 2 rows at a time.
@@ -245,11 +357,14 @@ struct PackInfo {
     int first_item[kGroups] = {}, items[kGroups] = {};
     int first_tile[kGroups] = {}, tiles[kGroups] = {};
     size_t gsmem[kGroups] = {};   // dynamic shared bytes the group's launch needs
+    int stage[kGroups] = {};      // pipelined groups: bytes of one staging slot
 };
 
 // Validate one item and write it as a device work item for tile shape (tw, th); smem gets
-// the dynamic shared bytes it needs (see pack_into for smem_cap).
-static kr_status build_item(const kr_work_t &w, int tw, int th, int smem_cap, WorkItem &it, size_t &smem)
+// the dynamic shared bytes it needs (see pack_into for smem_cap). pipe: the 3-channel
+// resample kinds run on the pipelined kernel, whose staging slot pack_into sizes per group
+// from the items' largest raw boxes (foot_budget).
+static kr_status build_item(const kr_work_t &w, int tw, int th, int smem_cap, bool pipe, WorkItem &it, size_t &smem)
 {
     if (w.src.batch != 1 || w.dst.batch != 1) return KR_ERR_INVALID_ARG;
     std::memset(&it, 0, sizeof(it));
@@ -281,6 +396,17 @@ static kr_status build_item(const kr_work_t &w, int tw, int th, int smem_cap, Wo
         const bool rows16 = ((uintptr_t)d.src & 15) == 0 && (d.spitch & 15) == 0;
         if (rows16) it.flags |= ITEM_ROWS16;
         if (d.replicate) it.flags |= ITEM_REPLICATE;
+        if (pipe && d.cin == 3) {
+            // raw boxes by bulk row copies (16-byte aligned rows), else taps from global memory
+            long long need = 0;
+            if (rows16 && bud.cols > 0 && bud.rows > 0 && bud.cols < 1000000 && bud.rows < 1000000)
+                need = 16LL * ((15 + bud.cols * 3 + 15) / 16) * bud.rows + 16;
+            if (rows16) it.flags |= ITEM_RAW;
+            it.foot_budget = (int)std::min<long long>(need, 1 << 30);
+            it.region_b = 0;
+            it.tiles_x = (it.w + tw - 1) / tw;
+            return KR_OK;
+        }
         if (d.cin == 3 && rows16 && bud.a > 0 && bud.fits) {
             // bulk row copies and raw taps: region A holds the item's largest box (plus
             // the 16 bytes a last pixel pair may touch), region B only the output tile
@@ -318,15 +444,17 @@ static kr_status build_item(const kr_work_t &w, int tw, int th, int smem_cap, Wo
 // of every launch (the residency the caller wants): an item whose boxes need more stages
 // only the tiles whose box fits what is left next to its output stage, and its other tiles
 // read their taps from global memory.
-static kr_status pack_into(const kr_work_t *items, int n, int tw, int th, int smem_cap, WorkItem *out,
-                           int *prefix, PackInfo &P)
+static kr_status pack_into(const kr_work_t *items, int n, int cfg, int smem_cap, WorkItem *out, int *prefix,
+                           PackInfo &P)
 {
     P = PackInfo();
+    const int tw = g_cfgs[cfg].tw, th = g_cfgs[cfg].th;
+    const bool pipe = cfg == 0;
     // pass 1: validate, count the items of each kind
     for (int i = 0; i < n; ++i) {
         WorkItem it;
         size_t sm;
-        kr_status st = build_item(items[i], tw, th, smem_cap, it, sm);
+        kr_status st = build_item(items[i], tw, th, smem_cap, pipe, it, sm);
         if (st != KR_OK) return st;
         P.items[group_of(it.kind)]++;
     }
@@ -336,12 +464,21 @@ static kr_status pack_into(const kr_work_t *items, int n, int tw, int th, int sm
     for (int i = 0; i < n; ++i) {
         WorkItem it;
         size_t sm;
-        kr_status st = build_item(items[i], tw, th, smem_cap, it, sm);
+        kr_status st = build_item(items[i], tw, th, smem_cap, pipe, it, sm);
         if (st != KR_OK) return st;
         const int g = group_of(it.kind);
         out[P.first_item[g] + fill[g]++] = it;
-        P.gsmem[g] = std::max(P.gsmem[g], sm);
-        P.smem = std::max(P.smem, sm);
+        if (uses_pipe(cfg, g)) {
+            // the slot holds the group's largest raw box, within what the cap leaves next to the
+            // unit stages; tiles with larger boxes read their taps from global memory
+            const long long cap = ((long long)smem_cap - (long long)pipe_smem(it.kind, 0)) / kPipeStages;
+            const int slot = (int)(std::min<long long>(it.foot_budget, std::max(cap, 0LL)) & ~127LL);
+            P.stage[g] = std::max(P.stage[g], slot);
+            P.gsmem[g] = pipe_smem(it.kind, P.stage[g]);
+        } else {
+            P.gsmem[g] = std::max(P.gsmem[g], sm);
+            P.smem = std::max(P.smem, sm);
+        }
         P.opmask |= 1 << items[i].op;
         P.out_px += (double)it.h * it.w;
     }
@@ -367,11 +504,11 @@ struct Packed {
     PackInfo info;
 };
 
-static kr_status pack_items(const kr_work_t *items, int n, int tw, int th, int smem_cap, Packed &P)
+static kr_status pack_items(const kr_work_t *items, int n, int cfg, int smem_cap, Packed &P)
 {
     P.items.resize(n);
     P.prefix.resize(n + 1);
-    return pack_into(items, n, tw, th, smem_cap, P.items.data(), P.prefix.data(), P.info);
+    return pack_into(items, n, cfg, smem_cap, P.items.data(), P.prefix.data(), P.info);
 }
 
 // Work-list image: header (with the group tables), items, tile prefix (the layout the
@@ -387,6 +524,7 @@ static void write_worklist_raw(const WorkItem *items, const int *prefix, int n, 
         h.items[g] = P.items[g];
         h.first_tile[g] = P.first_tile[g];
         h.tiles[g] = P.tiles[g];
+        h.stage_bytes[g] = P.stage[g];
     }
     std::memcpy(dst, &h, sizeof(h));
     std::memcpy(dst + sizeof(h), items, (size_t)n * sizeof(WorkItem));
@@ -485,9 +623,16 @@ static int sm_count()
 static cudaError_t prepare_kernel(int cfg, int g, size_t smem, int &occ)
 {
     const TileCfg &c = g_cfgs[cfg];
-    cudaError_t e = cudaFuncSetAttribute(c.kernels[g], cudaFuncAttributeMaxDynamicSharedMemorySize, c.max_smem);
+    int max_smem = c.max_smem;
+    if (uses_pipe(cfg, g)) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        max_smem -= (int)sizeof(PipeShared<kPipeTW, kPipeTH, kPipeStages>);
+    }
+    cudaError_t e = cudaFuncSetAttribute(c.kernels[g], cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.kernels[g], kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c.kernels[g], threads_of(cfg, g), smem);
     if (e != cudaSuccess) return e;
     occ = std::max(occ, 1);
     return cudaSuccess;
@@ -537,7 +682,7 @@ static cudaError_t launch_kinds(const Launches &L, int cfg, void *ws, cudaStream
             e = cudaStreamWaitEvent(s, side->fork, 0);
         }
         if (e == cudaSuccess)
-            e = cudaLaunchKernel(g_cfgs[cfg].kernels[g], dim3(L.grid[g]), dim3(kThreads), args, L.smem[g], s);
+            e = cudaLaunchKernel(g_cfgs[cfg].kernels[g], dim3(L.grid[g]), dim3(threads_of(cfg, g)), args, L.smem[g], s);
         ++k;
     }
     if (side && L.count > 1)
@@ -625,7 +770,7 @@ static kr_status enqueue(const Packed &P, void *ws, int cfg, int ctas_per_sm, bo
                 cudaKernelNodeParams kp{};
                 kp.func = (void *)g_cfgs[cfg].kernels[k];
                 kp.gridDim = dim3(L.grid[k]);
-                kp.blockDim = dim3(kThreads);
+                kp.blockDim = dim3(threads_of(cfg, k));
                 kp.sharedMemBytes = (unsigned)L.smem[k];
                 kp.kernelParams = args;
                 cudaGraphNode_t kn = nullptr;
@@ -722,7 +867,7 @@ kr_status kr_batch_submit(const kr_work_t *items, int32_t n, void *workspace, si
     if (cfg < 0) {
         // the cached choice for this batch class, else configuration 0
         const int k0 = ctas ? ctas : kDefaultCtasPerSm;
-        if ((st = pack_items(items, n, g_cfgs[0].tw, g_cfgs[0].th, smem_cap_for(0, k0), P)) != KR_OK) return st;
+        if ((st = pack_items(items, n, 0, smem_cap_for(0, k0), P)) != KR_OK) return st;
         const std::string key = class_key(P, n);
         int c = 0, k = k0;
         {
@@ -731,12 +876,12 @@ kr_status kr_batch_submit(const kr_work_t *items, int32_t n, void *workspace, si
             if (it != g_tune.end()) { c = it->second.first; if (!ctas) k = it->second.second; }
         }
         if (c != 0 || k != k0)
-            if ((st = pack_items(items, n, g_cfgs[c].tw, g_cfgs[c].th, smem_cap_for(c, k), P)) != KR_OK) return st;
+            if ((st = pack_items(items, n, c, smem_cap_for(c, k), P)) != KR_OK) return st;
         cfg = c;
         ctas = k;
     } else {
         if (!ctas) ctas = kDefaultCtasPerSm;
-        if ((st = pack_items(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th, smem_cap_for(cfg, ctas), P)) != KR_OK)
+        if ((st = pack_items(items, n, cfg, smem_cap_for(cfg, ctas), P)) != KR_OK)
             return st;
     }
     // every item must fit in shared memory at this tile shape
@@ -758,8 +903,7 @@ kr_status kr_batch_submit_noalloc(const kr_work_t *items, int32_t n, const kr_ba
 
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     PackInfo P;
-    kr_status st = pack_into(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th,
-                             smem_cap_for(cfg, ctas ? ctas : kDefaultCtasPerSm), g_noalloc_items,
+    kr_status st = pack_into(items, n, cfg, smem_cap_for(cfg, ctas ? ctas : kDefaultCtasPerSm), g_noalloc_items,
                              g_noalloc_prefix, P);
     if (st != KR_OK) return st;
     if (P.smem > (size_t)g_cfgs[cfg].max_smem) return KR_ERR_UNSUPPORTED;
@@ -802,7 +946,7 @@ kr_status kr_autotune_batch(const kr_work_t *items, int32_t n, void *workspace, 
         for (int k : kCands) {
             // each residency target packs the batch with its own shared-memory cap
             Packed P;
-            kr_status st = pack_items(items, n, g_cfgs[cfg].tw, g_cfgs[cfg].th, smem_cap_for(cfg, k), P);
+            kr_status st = pack_items(items, n, cfg, smem_cap_for(cfg, k), P);
             if (st == KR_ERR_NO_SPACE) continue;   // an output stage alone exceeds the cap
             if (st != KR_OK) { result = st; break; }
             if (key.empty()) key = class_key(P, n);   // the class does not depend on cfg or k

@@ -454,7 +454,7 @@ struct TileInfo {
                               // every tap is clamped into it
 };
 
-// The staging decision of a tile, taken once by the planning thread.
+// The staging decision of a tile.
 enum { TD_ZERO = 1, TD_STAGED = 2, TD_RAWBOX = 4, TD_FAST = 8, TD_TMA = 16, TD_BULK = 32 };
 struct TileDec {
     int rows, cols;   // box size
@@ -469,7 +469,6 @@ template <int TW, int TH> struct TileShared {
     uint32_t mbar_phase;   // parity of the barrier's next phase
     int32_t mbar_ok;       // 0 after a wait ran out twice: the barrier is not used again
     TileInfo ti;
-    TileDec td;
     int cx0[TW];     // column tap x0
     int cqd[TW];     // q | (x1 - x0) << 16
     float cf[TW];    // fp32 weight of x1

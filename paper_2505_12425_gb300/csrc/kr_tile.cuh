@@ -9,9 +9,9 @@ namespace kr {
 // ---------------------------------------------------------------------------
 // The tile engine.
 // ---------------------------------------------------------------------------
-// The staging decision for the planned box ti (run by the planning thread; see process_tile).
+// The staging decision for the planned box ti; every thread takes it from the shared plan.
 template <int OP, int CIN, bool ROWS, bool FRESH, int TW, int TH>
-__device__ __forceinline__ void decide_staging(const Job &J, TileShared<TW, TH> &ts)
+__device__ __forceinline__ TileDec decide_staging(const Job &J, const TileShared<TW, TH> &ts)
 {
     const TileInfo &ti = ts.ti;
     TileDec d;
@@ -50,7 +50,7 @@ __device__ __forceinline__ void decide_staging(const Job &J, TileShared<TW, TH> 
     d.rstride = use_tma ? 16 * J.tin_nc : use_bulk ? 16 * d.bnc : d.srow;
     d.flags = (zero_tile ? TD_ZERO : 0) | (staged ? TD_STAGED : 0) | (rawbox ? TD_RAWBOX : 0) | (fast ? TD_FAST : 0) |
               (use_tma ? TD_TMA : 0) | (use_bulk ? TD_BULK : 0);
-    ts.td = d;
+    return d;
 }
 
 // ROWS: the bulk row-copy staging is compiled in. FRESH: the CTA runs this one tile, and the
@@ -91,7 +91,6 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             ti.fx1 = ts.cx0[nx - 1] + (ts.cqd[nx - 1] >> 16);
             ti.fy0 = ts.ry0[0];
             ti.fy1 = ts.ry0[ny - 1] + (ts.rqd[ny - 1] >> 16);
-            decide_staging<OP, CIN, ROWS, FRESH>(J, ts);
         }
     } else if (warp == 0) {
         // Lanes 0..3 map one tile corner each; the box is their hull, one pixel wider
@@ -136,13 +135,12 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             ti.fast = fast;
             ti.zero = zero;
             ti.clamp = clamp;
-            decide_staging<OP, CIN, ROWS, FRESH>(J, ts);
         }
     }
     __syncthreads();
-    // The planning thread's staging decision.
+    // Every thread derives the staging decision from the planned box (no extra barrier).
     const int fx0 = ti.fx0, fx1 = ti.fx1, fy0 = ti.fy0, fy1 = ti.fy1;
-    const TileDec dec = ts.td;
+    const TileDec dec = decide_staging<OP, CIN, ROWS, FRESH>(J, ts);
     const int rows = dec.rows, cols = dec.cols, sw = dec.sw, bnc = dec.bnc;
     const bool zero_tile = (dec.flags & TD_ZERO) != 0;
     bool staged = (dec.flags & TD_STAGED) != 0;
