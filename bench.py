@@ -70,6 +70,9 @@ def kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
+NOMINAL_HBM_GBS = 8000.0   # the chip's nominal HBM bandwidth (~8 TB/s), beside the measured copy
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -215,7 +218,7 @@ def pitched(torch, img, dev, align=64):
     return v
 
 
-def ragged_compare(torch, kr, dev, reps=20):
+def ragged_compare(torch, kr, dev, peak=None, reps=20):
     """256 warps (sides log-uniform 64..2048, output 0.25-2x, pitched sources): one persistent
     graph-replayed launch vs 256 per-image launches. Returns a summary dict."""
     spec = inputs.ragged_batch(1003, 256)
@@ -265,7 +268,17 @@ def ragged_compare(torch, kr, dev, reps=20):
         res[name] = {"ms_p50": round(statistics.median(times), 4),
                      "ms_p99": round(times[min(len(times) - 1, int(0.99 * len(times)))], 4),
                      "gpx_s": round(out_px / (statistics.median(times) * 1e-3) / 1e9, 3)}
-    res.update({"items": 256, "out_px": out_px, "tile_config": list(kr.kr_tile_config_shape(cfg)),
+    t = json.load(open(os.path.join(ROOT, "tests", "golden", "bench_touched.json")))["extra"]["ragged_256_warps_u8"]
+    alg = sum(t["touched_bytes"]) + sum(t["out_bytes"])
+    alg_sec = sum(t["touched_sector_bytes"]) + sum(t["out_bytes"])
+    for name in ("batched", "per_image"):
+        gbs = alg / (res[name]["ms_p50"] * 1e-3) / 1e9
+        res[name]["GB_s"] = round(gbs, 1)
+        if peak:
+            res[name]["frac_of_measured_hbm"] = round(gbs / peak, 3)
+            res[name]["frac_of_measured_hbm_sector"] = round(alg_sec / (res[name]["ms_p50"] * 1e-3) / 1e9 / peak, 3)
+    res.update({"alg_bytes": alg, "alg_sector_bytes": alg_sec,
+                "items": 256, "out_px": out_px, "tile_config": list(kr.kr_tile_config_shape(cfg)),
                 "ctas_per_sm": ctas, "launches_batched": 1, "launches_per_image": 256,
                 "speedup_p50": round(res["per_image"]["ms_p50"] / res["batched"]["ms_p50"], 3)})
     return res
@@ -374,6 +387,91 @@ def next_rows(torch, kr, dev, imgs_dev, peak, reps=50):
         res[name] = {"ms": round(ms, 4), "alg_bytes": alg[name], "GB_s": round(gbs, 1),
                      "frac_of_measured_hbm": round(gbs / peak, 3), "gpx_s": round(opx / (ms * 1e-3) / 1e9, 1)}
     return res
+
+
+def l2_flush(torch, dev, buf=[]):
+    """Write a buffer twice the size of L2 so that the next launch reads from HBM."""
+    if not buf:
+        buf.append(torch.empty(256 << 20, dtype=torch.uint8, device=dev))
+    buf[0].fill_(1)
+
+
+def small_and_strong_downscale(torch, kr, dev, peak, reps=30):
+    """The two other resize workloads, bilinear:
+    c1  640x480 -> 320x240 u8 over 256 distinct uniform frames (295 MB of sources and
+        outputs, more than L2): one launch per frame (launch-bound: the work of a launch is
+        1.15 MB) and one launch over all 256 frames;
+    c3  16 uniform 3840x2160 -> 224x224 normalised planar f32 NCHW, one launch, L2 flushed
+        before every timed launch (its touched bytes would otherwise stay in L2).
+    Algorithmic bytes = output + the source bytes the taps read (the oracle's bitmaps,
+    tests/golden/bench_touched.json), pixel- and 32-byte-sector-granular."""
+    lib = kr.load()
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    extra = json.load(open(os.path.join(ROOT, "tests", "golden", "bench_touched.json")))["extra"]
+    out = {}
+    # c1
+    n1 = 256
+    src = torch.from_numpy(inputs.uniform_batch(1000, n1, 480, 640)).to(dev)
+    dst = torch.empty((n1, 240, 320, 3), dtype=torch.uint8, device=dev)
+    pp = kr.post()
+    sb, db = kr.image(src), kr.image(dst)
+    singles = [(kr.image(src[i]), kr.image(dst[i])) for i in range(n1)]
+    t1 = extra["c1_resize_u8_640x480_to_320x240"]
+    per_frame = 240 * 320 * 3 + t1["touched_bytes"]
+    per_frame_sec = 240 * 320 * 3 + t1["touched_sector_bytes"]
+
+    def one_per_frame():
+        for a, b in singles:
+            assert lib.kr_resize_bilinear(ctypes.byref(a), ctypes.byref(b), ctypes.byref(pp), st) == 0
+
+    def one_launch():
+        assert lib.kr_resize_bilinear(ctypes.byref(sb), ctypes.byref(db), ctypes.byref(pp), st) == 0
+
+    for name, fn, launches in (("per_frame_launches", one_per_frame, n1), ("one_launch", one_launch, 1)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        b.synchronize()
+        ms = a.elapsed_time(b) / reps
+        gbs = n1 * per_frame / (ms * 1e-3) / 1e9
+        out[f"c1_640x480_to_320x240_u8_{name}"] = {
+            "frames": n1, "launches": launches, "ms": round(ms, 4), "us_per_launch": round(ms * 1e3 / launches, 3),
+            "gpx_s": round(n1 * 240 * 320 / (ms * 1e-3) / 1e9, 2), "alg_bytes": n1 * per_frame, "GB_s": round(gbs, 1),
+            "frac_of_measured_hbm": round(gbs / peak, 3),
+            "frac_of_measured_hbm_sector": round(n1 * per_frame_sec / (ms * 1e-3) / 1e9 / peak, 3)}
+    del src, dst
+    # c3
+    src3 = torch.from_numpy(inputs.uniform_batch(1002, 16, 2160, 3840)).to(dev)
+    dst3 = torch.empty((16, 3, 224, 224), dtype=torch.float32, device=dev)
+    s3, d3 = kr.image(src3), kr.image(dst3, "chw")
+    pn = kr.post(mean=MEAN, std=STD)
+    t3 = extra["c3_resize_norm_f32_chw_3840x2160_to_224x224"]
+    ob = 224 * 224 * 3 * 4
+    for _ in range(3):
+        assert lib.kr_resize_bilinear(ctypes.byref(s3), ctypes.byref(d3), ctypes.byref(pn), st) == 0
+    times = []
+    for _ in range(reps):
+        l2_flush(torch, dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        assert lib.kr_resize_bilinear(ctypes.byref(s3), ctypes.byref(d3), ctypes.byref(pn), st) == 0
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    ms = statistics.median(times)
+    alg, alg_sec = 16 * (ob + t3["touched_bytes"]), 16 * (ob + t3["touched_sector_bytes"])
+    out["c3_16x3840x2160_to_224x224_norm_f32_chw"] = {
+        "images": 16, "launches": 1, "ms": round(ms, 4), "gpx_s": round(16 * 224 * 224 / (ms * 1e-3) / 1e9, 3),
+        "alg_bytes": alg, "alg_sector_bytes": alg_sec, "GB_s": round(alg / (ms * 1e-3) / 1e9, 1),
+        "frac_of_measured_hbm": round(alg / (ms * 1e-3) / 1e9 / peak, 3),
+        "frac_of_measured_hbm_sector": round(alg_sec / (ms * 1e-3) / 1e9 / peak, 3),
+        "l2": "flushed (256 MB write) before every timed launch"}
+    return out
 
 
 def cpu_baseline_sample(budget_s=12.0):
@@ -510,12 +608,14 @@ def run_gpu(args):
         alg_sec = n * ob + sum(touched[name]["touched_sector_bytes"][:n])
         gbs = alg / (per_op[name] * 1e-3) / 1e9
         breakdown[name] = {"ms": round(per_op[name], 4), "alg_bytes": alg, "GB_s": round(gbs, 1),
-                           "frac_of_measured_hbm": round(gbs / peak, 3), "alg_sector_bytes": alg_sec,
+                           "frac_of_measured_hbm": round(gbs / peak, 3),
+                           "frac_of_nominal_hbm": round(gbs / NOMINAL_HBM_GBS, 3), "alg_sector_bytes": alg_sec,
                            "frac_of_measured_hbm_sector": round(alg_sec / (per_op[name] * 1e-3) / 1e9 / peak, 3),
                            "share": round(per_op[name] / sum(per_op.values()), 3)}
     dom = breakdown[dominant]
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": dom["GB_s"], "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": dom["frac_of_measured_hbm"],
+                "frac_of_nominal_8tbs": dom["frac_of_nominal_hbm"],
                 "traffic": load_traffic(dominant), "alg_bytes_per_launch": dom["alg_bytes"]}
 
     # end to end through the public API: every step copies its inputs in from pinned host
@@ -576,7 +676,8 @@ def run_gpu(args):
            "steps": K_e2e}
 
     widening = next_rows(torch, kr, dev, imgs_dev, peak, reps=args.next_reps) if args.extras != "none" else None
-    ragged = ragged_compare(torch, kr, dev) if args.extras == "all" else None
+    ragged = ragged_compare(torch, kr, dev, peak) if args.extras == "all" else None
+    per_config = small_and_strong_downscale(torch, kr, dev, peak) if args.extras == "all" else None
     serving = serving_compare(torch, kr, dev, seconds=args.serve_seconds) if args.extras == "all" else None
     cpu = cpu_baseline_sample() if (rank == 0 and args.extras == "all") else None
     cpu_all = cpu_baseline_all_cores() if (rank == 0 and args.extras == "all") else None
@@ -592,7 +693,8 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "no flush: 199 MB of distinct source frames per step > 129 MB L2"},
             "roofline": roofline, "per_op": breakdown, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
-            "gpu_launches": K * len(ops), "next_rows": widening, "ragged": ragged, "serving": serving,
+            "gpu_launches": K * len(ops), "next_rows": widening, "per_config": per_config, "ragged": ragged,
+            "serving": serving,
             "clocks": clk.summary(),
         }
         print(json.dumps(line))

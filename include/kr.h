@@ -270,8 +270,15 @@ kr_status kr_batch_submit(const kr_work_t *items, int32_t n, void *workspace,
  *     reset by each call's copy): calls whose work may overlap on the GPU race,
  *     so serialise them (one stream, or events between streams);
  *   - calls no cudaMalloc, cudaFree, cudaHostAlloc or other allocating routine;
- *     the work list is copied from a fixed host array with cudaMemcpyAsync, and
- *     the call returns once that array has been read;
+ *     the work list is copied from a fixed (pageable) host array with
+ *     cudaMemcpyAsync, so the call first waits for the work already on `stream`
+ *     to finish (CUDA synchronises a pageable host-to-device copy with its stream)
+ *     and returns once that array has been read;
+ *   - a call made while `stream` is being captured into a CUDA graph returns
+ *     KR_ERR_UNSUPPORTED and enqueues nothing: a captured copy would read the
+ *     shared host array again at every replay, after later calls changed it;
+ *   - kr_shutdown forgets the looked-up device addresses: call it before a
+ *     cudaDeviceReset, after which the next call looks the address up again;
  *   - opts: tile_config < 0 means configuration 0 (no autotune lookup),
  *     ctas_per_sm as for kr_batch_submit, use_graph is ignored.
  * Results equal kr_batch_submit's bit for bit.
@@ -366,7 +373,21 @@ typedef struct {
  * exceed the budget or the arena; requests that arrive while others run are
  * admitted and launched as soon as a slot frees. Every request is validated
  * before anything runs (KR_ERR_INVALID_ARG / KR_ERR_NO_SPACE, nothing launched).
- * Returns when every output is complete. Results equal the single-image calls'.
+ * Returns when every request is complete or dropped. Results equal the
+ * single-image calls'.
+ *
+ * Every request ends in one of two states: completed (status KR_OK, t_done set,
+ * output in the arena) or dropped (status != KR_OK, t_done = -1, no output).
+ *   - a launch that fails drops its requests (status = the launch's status); their
+ *     bytes leave the budget, their arena space is freed and the run goes on;
+ *   - when recording a launch's completion event fails, the loop waits for that
+ *     launch's stream and completes its requests;
+ *   - an error reported by the device (an event query) stops the run: it returns
+ *     KR_ERR_CUDA and every request not completed is dropped with KR_ERR_CUDA;
+ *   - when retained outputs fill the arena so that the next request can never be
+ *     admitted, the run returns KR_ERR_NO_SPACE and drops the rest with it.
+ * The return value is KR_OK when the run went to the end (dropped requests are
+ * reported through their own status).
  */
 kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_serve_config_t *cfg,
                        kr_serve_result_t *results);
@@ -392,6 +413,34 @@ kr_status kr_device_errors(uint32_t *flags, int32_t clear);
 
 /* Release graphs, pinned staging and caches the library holds. Idempotent. */
 void kr_shutdown(void);
+
+/* ------------------------------------------------------------------------ */
+/* Test hooks: the failure paths, exercised without faulting a GPU. The     */
+/* paper has no counterpart of these.                                       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Bound, in nanoseconds, of the FIRST wait of every tile kernel (single-image and
+ * ragged) for its staged source box, on the current device; default 2e9. ns = 0
+ * makes that wait give up at once: every staged tile records KR_DEVERR_TMA_TIMEOUT,
+ * waits with the full 2 s bound for its copies to land and is abandoned without
+ * writing its output (tiles that stage nothing are written as usual). The second
+ * wait keeps its bound, so no kernel exits with a copy in flight. Applies to the
+ * kernels launched after the call.
+ */
+kr_status kr_debug_set_stage_wait_ns(uint64_t ns);
+
+/*
+ * Make one host-side step of kr_serve_run fail on every period-th time it runs
+ * (period 0 = never, the default); process-wide, until changed:
+ *   KR_FAULT_SUBMIT  a launch (batch or single request) returns KR_ERR_CUDA;
+ *   KR_FAULT_EVENT   recording a launch's completion event fails;
+ *   KR_FAULT_ADMIT   an arena allocation fails (as when the arena is full).
+ */
+#define KR_FAULT_SUBMIT 1
+#define KR_FAULT_EVENT 2
+#define KR_FAULT_ADMIT 3
+kr_status kr_debug_set_fault(int32_t site, int32_t period);
 
 #ifdef __cplusplus
 }

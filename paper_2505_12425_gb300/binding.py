@@ -107,6 +107,8 @@ def load():
         lib.kr_batch_submit_noalloc.argtypes = [P(KrWork), ctypes.c_int32, P(KrBatchOpts), ctypes.c_void_p]
         lib.kr_serve_run.argtypes = [P(KrRequest), ctypes.c_int32, P(KrServeConfig), P(KrServeResult)]
         lib.kr_device_errors.argtypes = [P(ctypes.c_uint32), ctypes.c_int32]
+        lib.kr_debug_set_stage_wait_ns.argtypes = [ctypes.c_uint64]
+        lib.kr_debug_set_fault.argtypes = [ctypes.c_int32, ctypes.c_int32]
         lib.kr_tile_config_count.argtypes = []
         lib.kr_tile_config_count.restype = ctypes.c_int32
         lib.kr_tile_config_shape.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32)]
@@ -122,7 +124,8 @@ def load():
         lib.kr_shutdown.restype = None
         for f in ("kr_resize_bilinear", "kr_warp_affine", "kr_warp_perspective", "kr_rgb_to_gray", "kr_resize_nearest",
                   "kr_flip_horizontal", "kr_sobel", "kr_resize_area", "kr_batch_submit",
-                  "kr_batch_submit_noalloc", "kr_serve_run", "kr_device_errors",
+                  "kr_batch_submit_noalloc", "kr_serve_run", "kr_device_errors", "kr_debug_set_stage_wait_ns",
+                  "kr_debug_set_fault",
                   "kr_tile_config_shape", "kr_autotune_batch", "kr_autotune_save", "kr_autotune_load"):
             getattr(lib, f).restype = S
         _lib = lib
@@ -363,6 +366,21 @@ def kr_device_errors(clear: bool = True) -> int:
     v = ctypes.c_uint32()
     _check(load().kr_device_errors(ctypes.byref(v), 1 if clear else 0), "kr_device_errors")
     return v.value
+
+
+# sites of kr_debug_set_fault
+KR_FAULT_SUBMIT, KR_FAULT_EVENT, KR_FAULT_ADMIT = 1, 2, 3
+KR_STAGE_WAIT_NS_DEFAULT = 2_000_000_000
+
+
+def kr_debug_set_stage_wait_ns(ns: int):
+    """Bound of the tile kernels' first wait for a staged box (0: give up at once)."""
+    _check(load().kr_debug_set_stage_wait_ns(int(ns)), "kr_debug_set_stage_wait_ns")
+
+
+def kr_debug_set_fault(site: int, period: int):
+    """Make a host-side step of kr_serve_run fail every period-th time (0: never)."""
+    _check(load().kr_debug_set_fault(int(site), int(period)), "kr_debug_set_fault")
 
 
 def requests_array(reqs) -> ctypes.Array:

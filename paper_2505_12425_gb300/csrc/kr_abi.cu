@@ -359,6 +359,17 @@ const char *kr_status_string(kr_status s)
 
 const char *kr_last_error(void) { return g_last_error; }
 
+kr_status kr_debug_set_stage_wait_ns(uint64_t ns)
+{
+    cudaError_t e = set_stage_wait_ns_ops(ns);
+    if (e == cudaSuccess) e = set_stage_wait_ns_batch(ns);
+    if (e != cudaSuccess) {
+        set_last_error("kr_debug_set_stage_wait_ns", e);
+        return KR_ERR_CUDA;
+    }
+    return KR_OK;
+}
+
 kr_status kr_device_errors(uint32_t *flags, int32_t clear)
 {
     if (!flags) return KR_ERR_INVALID_ARG;

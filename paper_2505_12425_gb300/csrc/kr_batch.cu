@@ -140,6 +140,7 @@ __device__ __forceinline__ Job job_of(const WorkItem &it)
     J.tout = nullptr;
     J.zimg = 0;
     J.err = &g_kr_batch_err;
+    J.wait_ns = g_kr_stage_wait_ns;
 #pragma unroll
     for (int k = 0; k < 6; ++k) J.M[k] = it.M[k];
 #pragma unroll
@@ -900,6 +901,15 @@ kr_status kr_batch_submit_noalloc(const kr_work_t *items, int32_t n, const kr_ba
     const int ctas = opts ? opts->ctas_per_sm : 0;
     if (cfg >= kNumCfgs || ctas < 0) return KR_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
+    // under capture the pageable copy would become a graph node reading g_noalloc_host at
+    // every replay, after later calls have rewritten it
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce != cudaSuccess) {
+        set_last_error("kr_batch_submit_noalloc", ce);
+        return KR_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return KR_ERR_UNSUPPORTED;
 
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     PackInfo P;
@@ -1030,10 +1040,15 @@ kr_status kr_autotune_load(const char *path)
 
 void kr_shutdown(void)
 {
-    std::lock_guard<std::mutex> lk(g_mu);
-    for (auto &kv : g_ctx) free_ctx(kv.second);
-    g_ctx.clear();
-    g_tune.clear();
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        for (auto &kv : g_ctx) free_ctx(kv.second);
+        g_ctx.clear();
+        g_tune.clear();
+    }
+    // the allocation-free path looks its array's device address up again on its next call
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    for (int d = 0; d < kMaxDevices; ++d) g_noalloc_dev[d] = nullptr;
 }
 
 }  // extern "C"

@@ -68,6 +68,7 @@ struct Job {
     const CUtensorMap *tout;  // destination map, box = one output tile; null = 128-bit stores
     int32_t zimg;             // image coordinate of this job in both maps
     unsigned *err;            // device error flags (bit 0: a bounded TMA wait ran out)
+    uint64_t wait_ns;         // bound of the first wait for a staged box (0: give up at once)
     float M[9];           // destination -> source map (warp: 2x3; perspective: 3x3), row-major
     float scale[3];       // f32: out = v255 * scale[c] + bias[c]
     float bias[3];
@@ -487,13 +488,15 @@ template <int TW, int TH> __device__ __forceinline__ void tile_shared_init(TileS
     }
 }
 
-// One thread waits (bounded) for the current phase of the staging barrier and records the
-// outcome in ti.tma_ok. A wait that runs out sets error bit 0 and waits once more for the
-// copies to land before the tile is abandoned; if that runs out too the barrier is retired.
-template <int TW, int TH> __device__ __forceinline__ void stage_wait(TileShared<TW, TH> &ts, unsigned *err)
+// One thread waits (bounded by first_ns; 0 gives up at once) for the current phase of the
+// staging barrier and records the outcome in ti.tma_ok. A wait that runs out sets error bit 0
+// and waits once more (bounded by kTmaWaitNs) for the copies to land before the tile is
+// abandoned; if that runs out too the barrier is retired.
+template <int TW, int TH>
+__device__ __forceinline__ void stage_wait(TileShared<TW, TH> &ts, unsigned *err, uint64_t first_ns)
 {
     const uint32_t ph = ts.mbar_phase;
-    bool ok = mbar_wait_bounded(&ts.mbar, ph, kTmaWaitNs);
+    bool ok = first_ns != 0 && mbar_wait_bounded(&ts.mbar, ph, first_ns);
     ts.ti.tma_ok = ok ? 1 : 0;
     if (!ok) {
         atomicOr(err, 1u);

@@ -114,7 +114,8 @@ bool warp_allows_fast(const float *M, int h, int w);
 
 // Device error flags of the per-operation kernels (synchronous read, optional clear).
 cudaError_t device_error_flags(unsigned *flags, bool clear);
-// Bound of the first staging wait of the pipelined ragged kernels.
+// Bound of the first wait for a staged box (per-operation kernels; ragged kernels).
+cudaError_t set_stage_wait_ns_ops(unsigned long long ns);
 cudaError_t set_stage_wait_ns_batch(unsigned long long ns);
 cudaError_t batch_error_flags(unsigned *flags, bool clear);
 

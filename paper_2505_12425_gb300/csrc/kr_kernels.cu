@@ -20,6 +20,10 @@ constexpr int kTH = 32;
 // Device error flags of the per-operation kernels (bit 0: a bounded TMA wait ran out).
 static __device__ unsigned g_kr_device_err;
 
+// Bound of the first wait for a tile's staged box (0: give up at once); the second wait, for
+// copies still in flight, always has the full bound.
+static __device__ unsigned long long g_kr_stage_wait_ns = kTmaWaitNs;
+
 
 // Largest raw box (bytes of 16-byte chunk rows) a 3-channel launch stages.
 constexpr long long kRawBoxCap = 56 * 1024;
@@ -84,6 +88,7 @@ __global__ void __launch_bounds__(kThreads, resample_min_ctas<OP, OUTK>()) resam
     J.tout = p.has_tout ? &p.tout : nullptr;
     J.zimg = z;
     J.err = &g_kr_device_err;
+    J.wait_ns = g_kr_stage_wait_ns;
 #pragma unroll
     for (int k = 0; k < 9; ++k) J.M[k] = OP != OP_RESIZE ? p.M[z][k] : 0.f;
 #pragma unroll
@@ -464,6 +469,11 @@ cudaError_t device_error_flags(unsigned *flags, bool clear)
         e = cudaMemcpyToSymbol(g_kr_device_err, &zero, sizeof(unsigned));
     }
     return e;
+}
+
+cudaError_t set_stage_wait_ns_ops(unsigned long long ns)
+{
+    return cudaMemcpyToSymbol(g_kr_stage_wait_ns, &ns, sizeof(ns));
 }
 
 cudaError_t launch_gray(const GrayDesc &d, cudaStream_t stream)

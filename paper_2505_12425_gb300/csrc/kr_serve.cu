@@ -21,6 +21,7 @@
 //             time, their bytes leave the budget and their arena space is freed.
 // The caller reads outputs from the arena at the offsets reported per request.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -82,6 +83,18 @@ struct Launch {
     int slot = -1;
 };
 
+// Injected host-side failures (kr_debug_set_fault): per site, fail every period-th time.
+struct FaultSite {
+    std::atomic<int> period{0};
+    std::atomic<long long> count{0};
+    bool fire()
+    {
+        const int p = period.load(std::memory_order_relaxed);
+        return p > 0 && (count.fetch_add(1, std::memory_order_relaxed) + 1) % p == 0;
+    }
+};
+FaultSite g_fault[4];
+
 }  // namespace
 }  // namespace kr
 
@@ -135,6 +148,7 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
     }
 
     Arena arena(cfg->out_arena_bytes);
+    FaultSite &f_submit = g_fault[KR_FAULT_SUBMIT], &f_event = g_fault[KR_FAULT_EVENT], &f_admit = g_fault[KR_FAULT_ADMIT];
     std::vector<uint64_t> out_off(n, 0);
     std::deque<int> pending, admitted;
     std::deque<Launch> inflight;
@@ -153,6 +167,7 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
 
     // one request through its single-image call
     auto launch_alone = [&](const kr_work_t &w, cudaStream_t s) -> kr_status {
+        if (f_submit.fire()) return KR_ERR_CUDA;
         if (w.op == KR_OP_RESIZE) return kr_resize_bilinear(&w.src, &w.dst, nullptr, (kr_stream_t)s);
         if (w.op == KR_OP_WARP) return kr_warp_affine(&w.src, &w.dst, w.M, nullptr, (kr_stream_t)s);
         return kr_rgb_to_gray(&w.src, &w.dst, (kr_stream_t)s);
@@ -174,6 +189,28 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
         std::memcpy(w.M, r.M, sizeof(w.M));
     };
 
+    // a request leaves the run: completed (td >= 0) or dropped with status st
+    auto finish = [&](int i, double td, kr_status st) {
+        results[i].t_done = td;
+        results[i].status = st;
+        bytes_in_flight -= in_bytes[i] + out_bytes[i];
+        if (st != KR_OK || !cfg->retain_outputs) arena.release(out_off[i], out_bytes[i]);
+        if (st != KR_OK) {
+            results[i].t_launch = -1.0;
+            results[i].out_offset = -1;
+        }
+        ++done;
+    };
+    // a launch whose completion cannot be tracked by an event: wait for its stream
+    auto complete_now = [&](const std::vector<int> &ids, cudaStream_t s) -> cudaError_t {
+        const cudaError_t q = cudaStreamSynchronize(s);
+        if (q == cudaSuccess) {
+            const double td = now_s();
+            for (int i : ids) finish(i, td, KR_OK);
+        }
+        return q;
+    };
+
     while (status == KR_OK && done < n) {
         const double t = now_s();
         // arrivals
@@ -184,24 +221,24 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
             if (q == cudaErrorNotReady) { ++it; continue; }
             if (q != cudaSuccess) { e = q; status = KR_ERR_CUDA; break; }
             const double td = now_s();
-            for (int i : it->reqs) {
-                results[i].t_done = td;
-                bytes_in_flight -= in_bytes[i] + out_bytes[i];
-                if (!cfg->retain_outputs) arena.release(out_off[i], out_bytes[i]);
-                ++done;
-            }
+            for (int i : it->reqs) finish(i, td, KR_OK);
             if (it->slot >= 0) slot_busy[it->slot] = 0;
             event_pool.push_back(it->done);
             it = inflight.erase(it);
         }
         if (status != KR_OK) break;
         // admission, in arrival order
+        bool arena_full = false;
         while (!pending.empty()) {
             const int i = pending.front();
             const uint64_t need = in_bytes[i] + out_bytes[i];
             if (cfg->hbm_budget_bytes && bytes_in_flight + need > cfg->hbm_budget_bytes) break;
             uint64_t off;
-            if (!arena.alloc(out_bytes[i], off)) break;
+            if (f_admit.fire()) break;   // an injected failure: the request waits, as for a full arena
+            if (!arena.alloc(out_bytes[i], off)) {
+                arena_full = true;
+                break;
+            }
             out_off[i] = off;
             bytes_in_flight += need;
             results[i].t_admit = now_s();
@@ -211,7 +248,7 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
         }
         // nothing runs and the head request can never be admitted: the arena is full of
         // retained outputs
-        if (!pending.empty() && admitted.empty() && inflight.empty() && next_arrival == n) {
+        if (arena_full && !pending.empty() && admitted.empty() && inflight.empty() && next_arrival == n) {
             status = KR_ERR_NO_SPACE;
             break;
         }
@@ -223,6 +260,7 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
                 Launch L;
                 L.slot = k;
                 work.clear();
+                std::vector<int> alone_ok;   // requests of this slot already launched alone
                 const double tl = now_s();
                 kr_status st = KR_OK;
                 while (!admitted.empty() && (int)L.reqs.size() < cfg->max_batch) {
@@ -234,21 +272,38 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
                     if (cfg->policy == 2 && (int64_t)w.dst.width * w.dst.height >= direct_px) {
                         st = launch_alone(w, streams[k]);
                         if (st != KR_OK) break;
+                        alone_ok.push_back(i);
                     } else {
                         work.push_back(w);
                     }
                 }
                 if (st == KR_OK && !work.empty()) {
                     void *ws = (uint8_t *)cfg->workspaces + (size_t)k * cfg->ws_bytes_each;
-                    st = kr_batch_submit(work.data(), (int32_t)work.size(), ws, cfg->ws_bytes_each, nullptr,
-                                         (kr_stream_t)streams[k]);
+                    st = f_submit.fire() ? KR_ERR_CUDA
+                                         : kr_batch_submit(work.data(), (int32_t)work.size(), ws, cfg->ws_bytes_each,
+                                                           nullptr, (kr_stream_t)streams[k]);
                 }
-                if (st != KR_OK) { status = st; break; }
+                for (int i : L.reqs) results[i].t_launch = tl;
+                if (st != KR_OK) {
+                    // a launch failed: the requests launched alone before it complete (once
+                    // their stream is idle), the others of this slot are dropped
+                    e = cudaStreamSynchronize(streams[k]);
+                    if (e != cudaSuccess) { status = KR_ERR_CUDA; break; }
+                    const double td = now_s();
+                    for (int i : L.reqs)
+                        if (std::find(alone_ok.begin(), alone_ok.end(), i) != alone_ok.end()) finish(i, td, KR_OK);
+                        else finish(i, -1.0, st);
+                    continue;
+                }
                 L.done = event_pool.back();
                 event_pool.pop_back();
-                e = cudaEventRecord(L.done, streams[k]);
-                if (e != cudaSuccess) { status = KR_ERR_CUDA; break; }
-                for (int i : L.reqs) results[i].t_launch = tl;
+                e = f_event.fire() ? cudaErrorUnknown : cudaEventRecord(L.done, streams[k]);
+                if (e != cudaSuccess) {
+                    event_pool.push_back(L.done);
+                    e = complete_now(L.reqs, streams[k]);
+                    if (e != cudaSuccess) { status = KR_ERR_CUDA; break; }
+                    continue;
+                }
                 slot_busy[k] = 1;
                 inflight.push_back(std::move(L));
             }
@@ -262,14 +317,22 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
                 rr = (rr + 1) % K;
                 const double tl = now_s();
                 const kr_status st = launch_alone(w, s);
-                if (st != KR_OK) { status = st; break; }
+                results[i].t_launch = tl;
+                if (st != KR_OK) {
+                    finish(i, -1.0, st);
+                    continue;
+                }
                 Launch L;
                 L.reqs.push_back(i);
                 L.done = event_pool.back();
                 event_pool.pop_back();
-                e = cudaEventRecord(L.done, s);
-                if (e != cudaSuccess) { status = KR_ERR_CUDA; break; }
-                results[i].t_launch = tl;
+                e = f_event.fire() ? cudaErrorUnknown : cudaEventRecord(L.done, s);
+                if (e != cudaSuccess) {
+                    event_pool.push_back(L.done);
+                    e = complete_now(L.reqs, s);
+                    if (e != cudaSuccess) { status = KR_ERR_CUDA; break; }
+                    continue;
+                }
                 inflight.push_back(std::move(L));
             }
         }
@@ -277,9 +340,25 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
     if (status == KR_ERR_CUDA) set_last_error("kr_serve_run", e);
     for (auto &s : streams)
         if (s) cudaStreamSynchronize(s);
+    // a run that stopped early drops every request that did not complete
+    if (status != KR_OK)
+        for (int i = 0; i < n; ++i)
+            if (results[i].t_done < 0) {
+                results[i].status = status;
+                results[i].t_launch = -1.0;
+                results[i].out_offset = -1;
+            }
     for (auto &L : inflight) event_pool.push_back(L.done);
     for (auto ev : event_pool) cudaEventDestroy(ev);
     for (auto &s : streams)
         if (s) cudaStreamDestroy(s);
     return status;
+}
+
+extern "C" kr_status kr_debug_set_fault(int32_t site, int32_t period)
+{
+    if (site < KR_FAULT_SUBMIT || site > KR_FAULT_ADMIT || period < 0) return KR_ERR_INVALID_ARG;
+    kr::g_fault[site].period.store(period, std::memory_order_relaxed);
+    kr::g_fault[site].count.store(0, std::memory_order_relaxed);
+    return KR_OK;
 }

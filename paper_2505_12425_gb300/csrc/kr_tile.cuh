@@ -174,7 +174,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                 if (FRESH) tile_shared_init(ts);
                 mbar_expect_tx(&ts.mbar, (uint32_t)(16 * J.tin_nc * J.tin_br));
                 tma_load_3d(raw, J.tin, 4 * ((fx0 * CIN) >> 4), fy0, J.zimg, &ts.mbar);
-                stage_wait(ts, J.err);
+                stage_wait(ts, J.err, J.wait_ns);
             }
             __syncthreads();
             if (!ti.tma_ok) return;
@@ -205,7 +205,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                             bulk_load(raw + r * rstride + (c0 - xb0), J.src + (int64_t)y * J.spitch + c0,
                                       (uint32_t)(c1 - c0), &ts.mbar);
                     }
-                if (lane == 0) stage_wait(ts, J.err);
+                if (lane == 0) stage_wait(ts, J.err, J.wait_ns);
             } else if (!(fy0 >= 0 && fy1 < J.H && xb0 >= 0 && xb1 <= F)) {
                 const int L3 = J.W * CIN;
                 for (int r = warp - 1; r < rows; r += kWarps - 1) {

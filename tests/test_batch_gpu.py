@@ -227,12 +227,16 @@ def test_workspace_too_small_is_rejected():
 
 @pytest.mark.parametrize("pitched", [False, True])
 def test_ragged_256_warps_full_size(pitched):
-    """256 warps, sides log-uniform 64..2048, output scale 0.25-2x: the batch equals
-    256 single-image launches everywhere and the oracle on sampled items."""
+    """256 warps, sides log-uniform 64..2048, output scale 0.25-2x: every item of the batch
+    equals its single-image launch and the oracle (the oracle's calls run on a thread pool:
+    they release the interpreter lock)."""
+    import concurrent.futures as cf
+    import os
     spec = inputs.ragged_batch(1003, 256)
-    srcs, dsts, work = [], [], []
+    imgs, srcs, dsts, work = [], [], [], []
     for it in spec:
         img = inputs.uniform_image(it.seed, it.H, it.W, 3)
+        imgs.append(img)
         s = to_src(img, pitched)
         d = torch.empty((it.h, it.w, 3), dtype=torch.uint8, device=dev())
         srcs.append(s)
@@ -246,9 +250,7 @@ def test_ragged_256_warps_full_size(pitched):
         kr.kr_warp_affine(s, single, it.M)
         torch.cuda.synchronize()
         assert torch.equal(single, d), i
-    for i in (0, 17, 100, 255):
-        it = spec[i]
-        if it.h * it.w > 1_500_000:
-            continue
-        np.testing.assert_array_equal(dsts[i].cpu().numpy(),
-                                      oracle.warp_u8(srcs[i].cpu().numpy(), it.M, it.h, it.w))
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        refs = list(ex.map(lambda k: oracle.warp_u8(imgs[k], spec[k].M, spec[k].h, spec[k].w), range(len(spec))))
+    for i, ref in enumerate(refs):
+        np.testing.assert_array_equal(dsts[i].cpu().numpy(), ref, err_msg=f"item {i}")

@@ -114,3 +114,58 @@ def test_noalloc_refuses_more_items_than_its_array_holds():
     items = (kr.KrWork * n)()
     o = kr.KrBatchOpts(-1, 0, 0)
     assert lib.kr_batch_submit_noalloc(items, n, ctypes.byref(o), None) == 5   # KR_ERR_NO_SPACE
+
+
+def test_noalloc_with_exactly_the_maximum_item_count():
+    """KR_BATCH_NOALLOC_MAX_ITEMS small items fill the library's work-list array to its end:
+    every one of them must come out as kr_batch_submit makes it (bit for bit, u8)."""
+    dev = torch.device("cuda:0")
+    n = kr.KR_BATCH_NOALLOC_MAX_ITEMS
+    rng = np.random.default_rng(77)
+    srcs, dst_a, dst_b, work_a, work_b = [], [], [], [], []
+    for i in range(n):
+        img = torch.from_numpy(inputs.uniform_image(7700 + i, 8, 8, 3)).to(dev)
+        if i % 2 == 0:
+            a = torch.empty((8, 8, 1), dtype=torch.uint8, device=dev)
+            b = torch.full((8, 8, 1), 0x3C, dtype=torch.uint8, device=dev)
+            work_a.append(kr.work_item(kr.KR_OP_GRAY, img, a))
+            work_b.append(kr.work_item(kr.KR_OP_GRAY, img, b))
+        else:
+            h, w = int(rng.integers(3, 17)), int(rng.integers(3, 17))
+            a = torch.empty((h, w, 3), dtype=torch.uint8, device=dev)
+            b = torch.full((h, w, 3), 0x3C, dtype=torch.uint8, device=dev)
+            work_a.append(kr.work_item(kr.KR_OP_RESIZE, img, a))
+            work_b.append(kr.work_item(kr.KR_OP_RESIZE, img, b))
+        srcs.append(img)
+        dst_a.append(a)
+        dst_b.append(b)
+    ws = torch.empty(kr.kr_batch_workspace_size(n), dtype=torch.uint8, device=dev)
+    kr.kr_batch_submit(kr.work_array(work_a), ws)
+    kr.kr_batch_submit_noalloc(kr.work_array(work_b))
+    torch.cuda.synchronize()
+    for a, b in zip(dst_a, dst_b):
+        assert torch.equal(a, b)
+
+
+def test_noalloc_refuses_a_capturing_stream_and_leaves_the_capture_valid():
+    """A call on a stream under graph capture returns KR_ERR_UNSUPPORTED, enqueues nothing,
+    and the capture still ends with a valid (empty) graph."""
+    dev = torch.device("cuda:0")
+    srcs, _, dst_b, specs = _items(13, 3)
+    w = _work(srcs, dst_b, specs)
+    kr.kr_batch_submit_noalloc(w)            # the first call on the device does the set-up
+    torch.cuda.synchronize()
+    lib = kr.load()
+    o = kr.KrBatchOpts(-1, 0, 0)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    x = torch.zeros(4, device=dev)
+    with torch.cuda.graph(g, stream=s):
+        x.add_(1.0)
+        st = lib.kr_batch_submit_noalloc(w, len(w), ctypes.byref(o), ctypes.c_void_p(s.cuda_stream))
+        x.add_(1.0)
+    assert st == 2   # KR_ERR_UNSUPPORTED
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(x, torch.full((4,), 4.0, device=dev))
