@@ -284,24 +284,34 @@ def ragged_compare(torch, kr, dev, peak=None, reps=20):
     return res
 
 
-def serving_compare(torch, kr, dev, rates=(2000, 5000, 10000, 20000, 40000, 80000, 160000, 320000, 640000),
-                    seconds=1.0):
+SERVE_RATES = (2000, 5000, 10000, 20000, 40000, 80000, 160000, 200000, 210000, 220000, 225000, 230000, 235000,
+               240000, 250000, 260000, 280000, 320000)
+SERVE_STREAMS = 8            # launches in flight (the best of 2/4/8/16 for both per-image and size-aware)
+SERVE_DIRECT_PX = 1 << 18    # size-aware threshold: requests of at least this many output pixels launch alone
+
+
+def serving_compare(torch, kr, dev, rates=SERVE_RATES, seconds=1.0, grid=False):
     """Poisson request streams (sizes log-uniform 320..3840 x 240..2160, op uniform over
     resize / warp / gray) over a device-resident pool of 64 pitched images, 8 GB in-flight budget:
     continuous batching (policy 0) vs one launch per request (policy 1) vs size-aware continuous
-    batching (policy 2: requests of at least 2^20 output pixels launch alone)."""
+    batching (policy 2: requests of at least 2^18 output pixels launch alone at once, the smaller
+    ones share ragged launches on free slots), 8 streams each. Offered rates step
+    finely between the last rate every policy keeps up with and saturation. grid: also every
+    (max_batch, streams) of {16, 32, 64} x {2, 4, 8} for the two batching policies (streams only
+    for per-image launches) at the rates around saturation."""
     sizes = inputs.pool_sizes(1004, 64)
     pool = [pitched(torch, inputs.uniform_image(5000 + i, H, W, 3), dev) for i, (H, W) in enumerate(sizes)]
     arena = torch.empty(8 << 30, dtype=torch.uint8, device=dev)
-    out = {"pool_images": 64, "budget_bytes": 8 << 30, "seconds_per_rate": seconds, "streams": 4,
-           "max_batch": 64, "runs": []}
+    out = {"pool_images": 64, "budget_bytes": 8 << 30, "seconds_per_rate": seconds, "streams": SERVE_STREAMS,
+           "max_batch": 64, "size_aware_direct_px": SERVE_DIRECT_PX, "runs": []}
     for rate in rates:
         # the highest rates run for a shorter time (the stream and its host-side arrays scale with it)
         dur = seconds if rate <= 80000 else seconds * 80000 / rate * 2
         reqs = inputs.request_stream(1004, float(rate), dur, pool=64)
         px = sum(r.h * r.w for r in reqs)
         for policy in (0, 1, 2):
-            res = kr.kr_serve_run(reqs, pool, arena, budget_bytes=8 << 30, max_batch=64, streams=4, policy=policy)
+            res = kr.kr_serve_run(reqs, pool, arena, budget_bytes=8 << 30, max_batch=64, streams=SERVE_STREAMS,
+                                  policy=policy, direct_px=SERVE_DIRECT_PX if policy == 2 else 0)
             lat = np.array([res[i].t_done - r.t_arrival for i, r in enumerate(reqs)]) * 1e3
             t_end = max(res[i].t_done for i in range(len(reqs)))
             nb = len({round(res[i].t_launch, 9) for i in range(len(reqs))})
@@ -310,11 +320,32 @@ def serving_compare(torch, kr, dev, rates=(2000, 5000, 10000, 20000, 40000, 8000
                 "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
                 "p999_ms": round(float(np.percentile(lat, 99.9)), 3),
                 "gpx_s": round(px / t_end / 1e9, 3), "launches": nb, "mean_batch": round(len(reqs) / nb, 2)})
+    if grid:
+        for rate in (200000, 220000, 240000):
+            dur = seconds * 80000 / rate * 2
+            reqs = inputs.request_stream(1004, float(rate), dur, pool=64)
+            px = sum(r.h * r.w for r in reqs)
+            for policy in (0, 1, 2):
+                for streams in (2, 4, 8):
+                    for mb in ((16, 32, 64) if policy != 1 else (64,)):
+                        res = kr.kr_serve_run(reqs, pool, arena, budget_bytes=8 << 30, max_batch=mb, streams=streams,
+                                              policy=policy, direct_px=SERVE_DIRECT_PX if policy == 2 else 0)
+                        lat = np.array([res[i].t_done - r.t_arrival for i, r in enumerate(reqs)]) * 1e3
+                        t_end = max(res[i].t_done for i in range(len(reqs)))
+                        out["runs"].append({
+                            "rate": rate, "policy": ("batched", "per_image", "size_aware")[policy],
+                            "streams": streams, "max_batch": mb, "requests": len(reqs),
+                            "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                            "p99_ms": round(float(np.percentile(lat, 99)), 3), "gpx_s": round(px / t_end / 1e9, 3)})
     best = {}
-    for slo in (2.0, 5.0, 10.0):
+    for slo in (2.0, 5.0, 10.0, 20.0):
         for pol in ("batched", "per_image", "size_aware"):
             ok = [r for r in out["runs"] if r["policy"] == pol and r["p99_ms"] <= slo]
-            best[f"{pol}_gpx_s_at_p99<={slo:g}ms"] = max((r["gpx_s"] for r in ok), default=None)
+            top = max(ok, key=lambda r: r["gpx_s"], default=None)
+            best[f"{pol}_gpx_s_at_p99<={slo:g}ms"] = top["gpx_s"] if top else None
+            if top and "streams" in top:
+                best[f"{pol}_config_at_p99<={slo:g}ms"] = {"streams": top["streams"], "max_batch": top["max_batch"],
+                                                           "rate": top["rate"]}
     out["best"] = best
     return out
 
@@ -678,7 +709,8 @@ def run_gpu(args):
     widening = next_rows(torch, kr, dev, imgs_dev, peak, reps=args.next_reps) if args.extras != "none" else None
     ragged = ragged_compare(torch, kr, dev, peak) if args.extras == "all" else None
     per_config = small_and_strong_downscale(torch, kr, dev, peak) if args.extras == "all" else None
-    serving = serving_compare(torch, kr, dev, seconds=args.serve_seconds) if args.extras == "all" else None
+    serving = serving_compare(torch, kr, dev, seconds=args.serve_seconds, grid=args.serve_grid) \
+        if args.extras == "all" else None
     cpu = cpu_baseline_sample() if (rank == 0 and args.extras == "all") else None
     cpu_all = cpu_baseline_all_cores() if (rank == 0 and args.extras == "all") else None
 
@@ -759,6 +791,8 @@ def main():
     ap.add_argument("--clocks-dir", default=None,
                     help="directory for the raw nvidia-smi clock samples (default: a temporary one)")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="seconds of requests per serving rate")
+    ap.add_argument("--serve-grid", action="store_true",
+                    help="also sweep the serving loop's streams and batch size around saturation")
     ap.add_argument("--images", type=int, default=inputs.BENCH_IMAGES,
                     help="frames per step (the full workload is 32; fewer only for small profiling cases)")
     args = ap.parse_args()

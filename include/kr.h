@@ -332,10 +332,11 @@ typedef struct {
  * limit); max_batch: items per ragged launch; streams: launches in flight (the
  * library creates and destroys these streams and their events); policy: 0 =
  * continuous batching (kr_batch_submit on a free slot with every admitted
- * request), 1 = one launch per request, 2 = size-aware continuous batching (on
- * a free slot, every admitted request of at least direct_px output pixels is
- * launched alone and the others go into one kr_batch_submit, all on the slot's
- * stream: large images fill the GPU by themselves, small ones share a launch);
+ * request), 1 = one launch per request, 2 = size-aware continuous batching (every
+ * admitted request of at least direct_px output pixels is launched alone at once,
+ * round-robin over the streams as in policy 1; the smaller ones wait for a free
+ * slot and share one kr_batch_submit on its stream: large images fill the GPU by
+ * themselves, small ones share a launch);
  * workspaces / ws_bytes_each: policies 0 and 2
  * only, `streams` device workspaces of ws_bytes_each >=
  * kr_batch_workspace_size(max_batch) bytes, caller-owned; retain_outputs: 0 =

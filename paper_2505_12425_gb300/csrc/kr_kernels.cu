@@ -52,11 +52,11 @@ struct OpParams {
 
 // ROWS: instantiated for launches whose 3-channel boxes are staged by bulk row copies (no
 // tensor map, 16-byte aligned rows); the others do without that code.
-// CTAs per SM the register allocation leaves room for: u8 kinds 8 (32 registers), f32 kinds
-// 6 (40).
+// CTAs per SM the register allocation leaves room for: u8 kinds 8 (32 registers; the
+// perspective warp 6, 40), the f32 resize 6 (40), the f32 warps 5 (48: at 40 they spill).
 template <int OP, int OUTK> constexpr int resample_min_ctas()
 {
-    return (OUTK == OUT_F32 || OUTK == OUT_F32_GRAY) ? 6 : 8;
+    return (OUTK == OUT_F32 || OUTK == OUT_F32_GRAY) ? (OP == OP_RESIZE ? 6 : 5) : (OP == OP_PERSP ? 6 : 8);
 }
 
 template <int OP, int CIN, int OUTK, int TW, int TH, bool ROWS>

@@ -14,9 +14,9 @@
 //             streams overlap on the device;
 //             (policy 1) every admitted request is launched alone, round-robin over
 //             the K streams (the per-image baseline);
-//             (policy 2) as policy 0, but on the free slot's stream every admitted
-//             request of at least direct_px output pixels is launched alone and
-//             only the smaller ones share the ragged launch;
+//             (policy 2) size-aware: every admitted request of at least direct_px
+//             output pixels is launched alone as in policy 1, the smaller ones share
+//             ragged launches as in policy 0;
 //   completion an event per launch is polled; its requests get their completion
 //             time, their bytes leave the budget and their arena space is freed.
 // The caller reads outputs from the arena at the offsets reported per request.
@@ -140,7 +140,7 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
     kr_status status = KR_OK;
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking);
-    const int n_events = cfg->policy != 1 ? K : std::min(4096, std::max(K, n));
+    const int n_events = cfg->policy == 0 ? K : std::min(4096, std::max(K, n)) + (cfg->policy == 2 ? K : 0);
     for (int k = 0; k < n_events && e == cudaSuccess; ++k) {
         cudaEvent_t ev;
         e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -150,7 +150,7 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
     Arena arena(cfg->out_arena_bytes);
     FaultSite &f_submit = g_fault[KR_FAULT_SUBMIT], &f_event = g_fault[KR_FAULT_EVENT], &f_admit = g_fault[KR_FAULT_ADMIT];
     std::vector<uint64_t> out_off(n, 0);
-    std::deque<int> pending, admitted;
+    std::deque<int> pending, admitted, small;   // small: policy 2's requests waiting for a batch slot
     std::deque<Launch> inflight;
     std::vector<int> slot_busy(K, 0);
     std::vector<kr_work_t> work;
@@ -248,51 +248,77 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
         }
         // nothing runs and the head request can never be admitted: the arena is full of
         // retained outputs
-        if (arena_full && !pending.empty() && admitted.empty() && inflight.empty() && next_arrival == n) {
+        if (arena_full && !pending.empty() && admitted.empty() && small.empty() && inflight.empty() && next_arrival == n) {
             status = KR_ERR_NO_SPACE;
             break;
         }
         // launches
+        const int64_t direct_px = cfg->direct_px > 0 ? cfg->direct_px : (int64_t)1 << 20;
+        if (cfg->policy != 0) {
+            // per-image launches, round-robin over the streams, each tracked by its own event:
+            // every admitted request (policy 1), or those of at least direct_px output pixels
+            // (policy 2, the others wait for a batch slot)
+            while (!admitted.empty() && !event_pool.empty() && status == KR_OK) {
+                const int i = admitted.front();
+                admitted.pop_front();
+                kr_work_t w;
+                make_work(i, w);
+                if (cfg->policy == 2 && (int64_t)w.dst.width * w.dst.height < direct_px) {
+                    small.push_back(i);
+                    continue;
+                }
+                cudaStream_t st_s = streams[rr];
+                rr = (rr + 1) % K;
+                const double tl = now_s();
+                const kr_status st = launch_alone(w, st_s);
+                results[i].t_launch = tl;
+                if (st != KR_OK) {
+                    finish(i, -1.0, st);
+                    continue;
+                }
+                Launch L;
+                L.reqs.push_back(i);
+                L.done = event_pool.back();
+                event_pool.pop_back();
+                e = f_event.fire() ? cudaErrorUnknown : cudaEventRecord(L.done, st_s);
+                if (e != cudaSuccess) {
+                    event_pool.push_back(L.done);
+                    e = complete_now(L.reqs, st_s);
+                    if (e != cudaSuccess) status = KR_ERR_CUDA;
+                    continue;
+                }
+                inflight.push_back(std::move(L));
+            }
+            if (status != KR_OK) break;
+        }
         if (cfg->policy != 1) {
-            const int64_t direct_px = cfg->direct_px > 0 ? cfg->direct_px : (int64_t)1 << 20;
-            for (int k = 0; k < K && !admitted.empty(); ++k) {
+            // ragged batches: whenever a slot is free, the waiting requests (all admitted ones for
+            // policy 0, the small ones for policy 2) -- up to max_batch -- share one launch on
+            // the slot's stream
+            std::deque<int> &q = cfg->policy == 0 ? admitted : small;
+            for (int k = 0; k < K && !q.empty() && !event_pool.empty(); ++k) {
                 if (slot_busy[k]) continue;
                 Launch L;
                 L.slot = k;
                 work.clear();
-                std::vector<int> alone_ok;   // requests of this slot already launched alone
                 const double tl = now_s();
-                kr_status st = KR_OK;
-                while (!admitted.empty() && (int)L.reqs.size() < cfg->max_batch) {
-                    const int i = admitted.front();
-                    admitted.pop_front();
+                while (!q.empty() && (int)L.reqs.size() < cfg->max_batch) {
+                    const int i = q.front();
+                    q.pop_front();
                     kr_work_t w;
                     make_work(i, w);
                     L.reqs.push_back(i);
-                    if (cfg->policy == 2 && (int64_t)w.dst.width * w.dst.height >= direct_px) {
-                        st = launch_alone(w, streams[k]);
-                        if (st != KR_OK) break;
-                        alone_ok.push_back(i);
-                    } else {
-                        work.push_back(w);
-                    }
+                    work.push_back(w);
                 }
-                if (st == KR_OK && !work.empty()) {
-                    void *ws = (uint8_t *)cfg->workspaces + (size_t)k * cfg->ws_bytes_each;
-                    st = f_submit.fire() ? KR_ERR_CUDA
-                                         : kr_batch_submit(work.data(), (int32_t)work.size(), ws, cfg->ws_bytes_each,
-                                                           nullptr, (kr_stream_t)streams[k]);
-                }
+                void *ws = (uint8_t *)cfg->workspaces + (size_t)k * cfg->ws_bytes_each;
+                const kr_status st = f_submit.fire() ? KR_ERR_CUDA
+                                                     : kr_batch_submit(work.data(), (int32_t)work.size(), ws,
+                                                                       cfg->ws_bytes_each, nullptr,
+                                                                       (kr_stream_t)streams[k]);
                 for (int i : L.reqs) results[i].t_launch = tl;
                 if (st != KR_OK) {
-                    // a launch failed: the requests launched alone before it complete (once
-                    // their stream is idle), the others of this slot are dropped
-                    e = cudaStreamSynchronize(streams[k]);
-                    if (e != cudaSuccess) { status = KR_ERR_CUDA; break; }
-                    const double td = now_s();
-                    for (int i : L.reqs)
-                        if (std::find(alone_ok.begin(), alone_ok.end(), i) != alone_ok.end()) finish(i, td, KR_OK);
-                        else finish(i, -1.0, st);
+                    // the launch failed: its requests are dropped
+                    for (int i : L.reqs) finish(i, -1.0, st);
                     continue;
                 }
                 L.done = event_pool.back();
@@ -305,34 +331,6 @@ extern "C" kr_status kr_serve_run(const kr_request_t *reqs, int32_t n, const kr_
                     continue;
                 }
                 slot_busy[k] = 1;
-                inflight.push_back(std::move(L));
-            }
-        } else {
-            while (!admitted.empty() && !event_pool.empty()) {
-                const int i = admitted.front();
-                admitted.pop_front();
-                kr_work_t w;
-                make_work(i, w);
-                cudaStream_t s = streams[rr];
-                rr = (rr + 1) % K;
-                const double tl = now_s();
-                const kr_status st = launch_alone(w, s);
-                results[i].t_launch = tl;
-                if (st != KR_OK) {
-                    finish(i, -1.0, st);
-                    continue;
-                }
-                Launch L;
-                L.reqs.push_back(i);
-                L.done = event_pool.back();
-                event_pool.pop_back();
-                e = f_event.fire() ? cudaErrorUnknown : cudaEventRecord(L.done, s);
-                if (e != cudaSuccess) {
-                    event_pool.push_back(L.done);
-                    e = complete_now(L.reqs, s);
-                    if (e != cudaSuccess) { status = KR_ERR_CUDA; break; }
-                    continue;
-                }
                 inflight.push_back(std::move(L));
             }
         }

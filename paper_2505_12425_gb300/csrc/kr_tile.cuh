@@ -620,6 +620,22 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                             const uint8_t *s0 = raw + r0 * rstride + ph0 + (x0 - fx0);
                             const uint8_t *s1 = raw + r1 * rstride + ph1 + (x0 - fx0);
                             p00 = s0[0]; p01 = s0[dx]; p10 = s1[0]; p11 = s1[dx];
+                        } else if (CIN == 3 && !(OP != OP_RESIZE && J.replicate) && dx == 1 && dy == 1 &&
+                                   x0 >= 0 && x0 + 1 < J.W && y0 >= 0 && y0 + 2 < J.H &&
+                                   (((uintptr_t)J.src | (uintptr_t)J.spitch) & 3) == 0) {
+                            // both taps inside and both rows followed by a row of the image: each
+                            // row's pair from three aligned words (at most 11 bytes past the pair,
+                            // inside the next row), read as a raw pair
+                            const uint8_t *a = J.src + (int64_t)y0 * J.spitch + 3 * x0;
+                            const uint32_t *w0 = reinterpret_cast<const uint32_t *>((uintptr_t)a & ~(uintptr_t)3);
+                            const uint32_t *w1 = reinterpret_cast<const uint32_t *>((uintptr_t)(a + J.spitch) & ~(uintptr_t)3);
+                            const uint32_t sh8 = (uint32_t)(uintptr_t)a << 3;
+                            p00 = __funnelshift_r(__ldg(w0), __ldg(w0 + 1), sh8);
+                            p01 = __funnelshift_r(__ldg(w0 + 1), __ldg(w0 + 2), sh8);
+                            p10 = __funnelshift_r(__ldg(w1), __ldg(w1 + 1), sh8);
+                            p11 = __funnelshift_r(__ldg(w1 + 1), __ldg(w1 + 2), sh8);
+                            emit<CIN, OUTK, TAPS_RAW>(J, o, c, p00, p01, p10, p11, qx, qy, fx, fy);
+                            continue;
                         } else if (CIN == 3) {
                             const bool rp = OP != OP_RESIZE && J.replicate;
                             p00 = ldg_px3(J.src, J.spitch, J.H, J.W, y0, x0, rp);
