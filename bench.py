@@ -65,7 +65,7 @@ def kernel_source_sha() -> str:
     """Hash of the sources of the per-operation kernels (the tile engine and its launcher)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2505_12425_gb300", "csrc")
-    for f in ("kr_device.cuh", "kr_kernels.cu"):
+    for f in ("kr_device.cuh", "kr_quad.cuh", "kr_tile.cuh", "kr_kernels.cu"):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -218,7 +218,7 @@ def pitched(torch, img, dev, align=64):
     return v
 
 
-def ragged_compare(torch, kr, dev, peak=None, reps=20):
+def ragged_compare(torch, kr, dev, peak=None, reps=20, autotune=True):
     """256 warps (sides log-uniform 64..2048, output 0.25-2x, pitched sources): one persistent
     graph-replayed launch vs 256 per-image launches. Returns a summary dict."""
     spec = inputs.ragged_batch(1003, 256)
@@ -231,7 +231,9 @@ def ragged_compare(torch, kr, dev, peak=None, reps=20):
         work.append(kr.work_item(kr.KR_OP_WARP, s, d, M=it.M))
     arr = kr.work_array(work)
     ws = torch.empty(kr.kr_batch_workspace_size(len(arr)), dtype=torch.uint8, device=dev)
-    cfg, ctas = kr.kr_autotune_batch(arr, ws)
+    # autotune: the tuner's pick for this batch class (else tile configuration 0 at its default
+    # residency, a fixed launch for profiling)
+    cfg, ctas = kr.kr_autotune_batch(arr, ws) if autotune else (0, 0)
     out_px = sum(it.h * it.w for it in spec)
     lib = kr.load()
     single = []
@@ -240,7 +242,7 @@ def ragged_compare(torch, kr, dev, peak=None, reps=20):
         M = np.ascontiguousarray(it.M.reshape(-1), dtype=np.float32)
         single.append((si, di, pp, M, M.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    opts = kr.KrBatchOpts(-1, 0, 1)
+    opts = kr.KrBatchOpts(-1, 0, 1) if autotune else kr.KrBatchOpts(0, 0, 1)
 
     def batched():
         r = lib.kr_batch_submit(arr, len(arr), ctypes.c_void_p(ws.data_ptr()), ws.numel(), ctypes.byref(opts), st)
@@ -706,8 +708,10 @@ def run_gpu(args):
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(ms_e2e, 3),
            "steps": K_e2e}
 
-    widening = next_rows(torch, kr, dev, imgs_dev, peak, reps=args.next_reps) if args.extras != "none" else None
-    ragged = ragged_compare(torch, kr, dev, peak) if args.extras == "all" else None
+    widening = next_rows(torch, kr, dev, imgs_dev, peak, reps=args.next_reps) \
+        if args.extras in ("all", "next-rows") else None
+    ragged = ragged_compare(torch, kr, dev, peak) if args.extras == "all" else \
+        ragged_compare(torch, kr, dev, peak, autotune=False) if args.extras == "ragged" else None
     per_config = small_and_strong_downscale(torch, kr, dev, peak) if args.extras == "all" else None
     serving = serving_compare(torch, kr, dev, seconds=args.serve_seconds, grid=args.serve_grid) \
         if args.extras == "all" else None
@@ -785,8 +789,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-extras", action="store_true", help="skip the next rows, the ragged and serving comparisons and the CPU baseline")
-    ap.add_argument("--extras", choices=["all", "next-rows", "none"], default="all",
-                    help="which extra measurements follow the step: all, only the next rows, or none")
+    ap.add_argument("--extras", choices=["all", "next-rows", "ragged", "none"], default="all",
+                    help="which extra measurements follow the step: all, only the next rows, only the ragged "
+                         "batch (tile configuration 0, no autotuning), or none")
     ap.add_argument("--next-reps", type=int, default=50, help="timed launches per next row")
     ap.add_argument("--clocks-dir", default=None,
                     help="directory for the raw nvidia-smi clock samples (default: a temporary one)")

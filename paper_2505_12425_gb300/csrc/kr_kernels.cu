@@ -24,7 +24,6 @@ static __device__ unsigned g_kr_device_err;
 // copies still in flight, always has the full bound.
 static __device__ unsigned long long g_kr_stage_wait_ns = kTmaWaitNs;
 
-
 // Largest raw box (bytes of 16-byte chunk rows) a 3-channel launch stages.
 constexpr long long kRawBoxCap = 56 * 1024;
 
@@ -50,8 +49,6 @@ struct OpParams {
     float M[kMaxMPerLaunch][9];   // warp: 6 floats per image; perspective: 9
 };
 
-// ROWS: instantiated for launches whose 3-channel boxes are staged by bulk row copies (no
-// tensor map, 16-byte aligned rows); the others do without that code.
 // CTAs per SM the register allocation leaves room for: u8 kinds 8 (32 registers; the
 // perspective warp 6, 40), the f32 resize 6 (40), the f32 warps 5 (48: at 40 they spill).
 template <int OP, int OUTK> constexpr int resample_min_ctas()
@@ -59,6 +56,8 @@ template <int OP, int OUTK> constexpr int resample_min_ctas()
     return (OUTK == OUT_F32 || OUTK == OUT_F32_GRAY) ? (OP == OP_RESIZE ? 6 : 5) : (OP == OP_PERSP ? 6 : 8);
 }
 
+// ROWS: instantiated for launches whose 3-channel boxes are staged by bulk row copies (no
+// tensor map, 16-byte aligned rows); the others do without that code.
 template <int OP, int CIN, int OUTK, int TW, int TH, bool ROWS>
 __global__ void __launch_bounds__(kThreads, resample_min_ctas<OP, OUTK>()) resample_kernel(const __grid_constant__ OpParams p)
 {
@@ -342,7 +341,13 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
             // plus the 16 bytes that reading the last pixel pair may touch past it, region B
             // only the output tile; the rows come by one TMA copy per tile when the source
             // takes a map, else by bulk row copies when its rows are 16-byte aligned
-            const int nc = (15 + raw_cols * CIN + 15) / 16, br = raw_rows;
+            // The box row is padded to 4 mod 8 chunks when that fits: neighbouring staged rows are
+            // then 16 banks apart, and the two half-warps of the 4-pixel quad path, which read
+            // neighbouring rows, hit disjoint banks for unit-scale maps.
+            int nc = (15 + raw_cols * CIN + 15) / 16;
+            const int br = raw_rows;
+            const int ncp = nc + ((12 - nc % 8) % 8);
+            if (ncp <= 64 && 16LL * ncp * br + 16 <= kRawBoxCap) nc = ncp;
             if (encode_map(&p.tin, p.src, (int64_t)d.W * CIN, d.H, 1, nb, d.spitch, 0, d.sbatch, nc, br)) {
                 p.has_tin = 1;
                 p.tin_nc = nc;
