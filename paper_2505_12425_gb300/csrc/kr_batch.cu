@@ -141,6 +141,7 @@ __device__ __forceinline__ Job job_of(const WorkItem &it)
     J.zimg = 0;
     J.err = &g_kr_batch_err;
     J.wait_ns = g_kr_stage_wait_ns;
+    J.rm[0] = J.rm[1] = J.rm[2] = J.rm[3] = 0u;
 #pragma unroll
     for (int k = 0; k < 6; ++k) J.M[k] = it.M[k];
 #pragma unroll

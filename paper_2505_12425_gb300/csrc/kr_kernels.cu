@@ -44,6 +44,7 @@ struct OpParams {
     int32_t raw_taps;
     int32_t rows16;
     int32_t replicate;
+    uint32_t rm[4];   // resize: multiply-high reciprocals of 2w, 4w, 2h, 4h (0: divide)
     uint32_t fast_mask[(kMaxMPerLaunch + 31) / 32];   // warp: images whose map allows the fast path
     float scale[3], bias[3];
     float M[kMaxMPerLaunch][9];   // warp: 6 floats per image; perspective: 9
@@ -88,6 +89,8 @@ __global__ void __launch_bounds__(kThreads, resample_min_ctas<OP, OUTK>()) resam
     J.zimg = z;
     J.err = &g_kr_device_err;
     J.wait_ns = g_kr_stage_wait_ns;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) J.rm[k] = p.rm[k];
 #pragma unroll
     for (int k = 0; k < 9; ++k) J.M[k] = OP != OP_RESIZE ? p.M[z][k] : 0.f;
 #pragma unroll
@@ -290,6 +293,11 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
     p.w = d.w;
     p.chw = d.chw;
     p.replicate = d.replicate;
+    if (OP == OP_RESIZE && d.W < 32768 && d.w < 32768 && d.H < 32768 && d.h < 32768) {
+        // the axis tables' divisions by 2w, 4w, 2h, 4h as multiply-high (resize_axis_m)
+        const uint32_t den[4] = {2u * d.w, 4u * d.w, 2u * d.h, 4u * d.h};
+        for (int k = 0; k < 4; ++k) p.rm[k] = 0xFFFFFFFFu / den[k];
+    }
     for (int k = 0; k < 3; ++k) {
         p.scale[k] = d.scale[k];
         p.bias[k] = d.bias[k];

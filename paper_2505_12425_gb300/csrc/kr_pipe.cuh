@@ -122,34 +122,6 @@ __device__ __forceinline__ bool pipe_first_wait(uint64_t *mbar, uint32_t parity,
 // ---------------------------------------------------------------------------
 // Producer
 // ---------------------------------------------------------------------------
-// resize_axis for sizes below 2^15 with the divisions by den = 2 n_out and by 2 den done as a
-// multiply-high by mden = floor((2^32 - 1) / den) (m2den for 2 den) and one correction step:
-// for num < 2^32 the estimate floor(num mden / 2^32) is the quotient or one less.
-__device__ __forceinline__ void resize_axis_m(int i, int n_in, int n_out, uint32_t mden, uint32_t m2den, int &i0,
-                                              int &i1, int &q, float &f)
-{
-    const int num = (2 * i + 1) * n_in - n_out;
-    const uint32_t den = 2u * (uint32_t)n_out;
-    if (num <= 0) {
-        i0 = 0; q = 0; f = 0.f;
-    } else {
-        uint32_t k = __umulhi((uint32_t)num, mden);
-        uint32_t r = (uint32_t)num - k * den;
-        if (r >= den) { ++k; r -= den; }
-        if ((int)k >= n_in - 1) {
-            i0 = n_in - 1; q = 0; f = 0.f;
-        } else {
-            i0 = (int)k;
-            const uint32_t n2 = 4096u * r + den, d2 = 2u * den;
-            uint32_t qq = __umulhi(n2, m2den);
-            if (n2 - qq * d2 >= d2) ++qq;
-            q = (int)qq;
-            f = __fdiv_rn((float)r, (float)den);
-        }
-    }
-    i1 = min(i0 + 1, n_in - 1);
-}
-
 // Pol provides (warp-uniform):
 //   bool tile(int k, int lane, int &job, int &tx, int &ty)   the CTA's k-th tile (k = 0, 1, ...
 //                                                            in order), false past the last

@@ -76,13 +76,19 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         if (tid < TW) {
             int i0 = 0, i1 = 0, q = 0;
             float f = 0.f;
-            if (tid < nx) resize_axis(tx0 + tid, J.W, J.w, i0, i1, q, f);
+            if (tid < nx) {
+                if (J.rm[0]) resize_axis_m(tx0 + tid, J.W, J.w, J.rm[0], J.rm[1], i0, i1, q, f);
+                else resize_axis(tx0 + tid, J.W, J.w, i0, i1, q, f);
+            }
             ts.cx0[tid] = i0; ts.cqd[tid] = q | ((i1 - i0) << 16); ts.cf[tid] = f;
         } else if (tid < TW + TH) {
             const int r = tid - TW;
             int i0 = 0, i1 = 0, q = 0;
             float f = 0.f;
-            if (r < ny) resize_axis(ty0 + r, J.H, J.h, i0, i1, q, f);
+            if (r < ny) {
+                if (J.rm[0]) resize_axis_m(ty0 + r, J.H, J.h, J.rm[2], J.rm[3], i0, i1, q, f);
+                else resize_axis(ty0 + r, J.H, J.h, i0, i1, q, f);
+            }
             ts.ry0[r] = i0; ts.rqd[r] = q | ((i1 - i0) << 16); ts.rf[r] = f;
         }
         __syncthreads();
