@@ -627,10 +627,15 @@ static cudaError_t prepare_kernel(int cfg, int g, size_t smem, int &occ)
     const TileCfg &c = g_cfgs[cfg];
     int max_smem = c.max_smem;
     if (uses_pipe(cfg, g)) {
-        int dev = 0;
+        // everything the opt-in limit leaves next to the kernel's static shared memory
+        int dev = 0, optin = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        max_smem -= (int)sizeof(PipeShared<kPipeTW, kPipeTH, kPipeStages>);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa;
+        std::memset(&fa, 0, sizeof(fa));
+        cudaError_t e = cudaFuncGetAttributes(&fa, c.kernels[g]);
+        if (e != cudaSuccess) return e;
+        max_smem = (optin - (int)fa.sharedSizeBytes) & ~127;
     }
     cudaError_t e = cudaFuncSetAttribute(c.kernels[g], cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     if (e != cudaSuccess) return e;

@@ -476,10 +476,12 @@ __device__ __forceinline__ void pipe_consume(Pol &P, PipeShared<TW, TH, NS> &sh,
         const uint32_t obase = (uint32_t)(uintptr_t)(J.dst + (int64_t)ty0 * J.dpitch +
                                                      (chw ? (int64_t)tx0 * 4 : (int64_t)tx0 * dC * ES));
         const uint32_t opitch = (uint32_t)J.dpitch, oplane = (uint32_t)J.dplane;
-        const bool quad = mode == PM_STAGED && fast && nx == TW;
+        // staged fast tiles take the quad path, full width or not (quad_setup); zero tiles write
+        // the zero sample in the same layout
+        const bool quad = mode == PM_STAGED && fast;
 
         QuadTile T;
-        if (quad) quad_setup<OP, OUTK>(T, J, sl.cx0, sl.cqd, sl.cf, tx0, fx0, fy0, rstride, sraw, rph, cb);
+        if (quad) quad_setup<OP, OUTK>(T, J, sl.cx0, sl.cqd, sl.cf, tx0, fx0, fy0, rstride, sraw, rph, cb, nx);
 
         for (int ra = UR * warp; ra < ny; ra += UR * NWARP) {
             const uint32_t ub = wbuf + (uint32_t)((u & 1) * unit_bytes);
@@ -507,62 +509,22 @@ __device__ __forceinline__ void pipe_consume(Pol &P, PipeShared<TW, TH, NS> &sh,
                 if (quad) {
                     quad_row<OP, OUTK>(T, J, sl.ry0, sl.rqd, sl.rf, r, ty0, fy0, rstride, sraw, chw, row_off(hr, 0),
                                        chw ? row_off(hr, 1) : 0u, chw ? row_off(hr, 2) : 0u, cb);
+                } else if (mode == PM_ZERO) {
+                    // every tap lies outside the image: the zero sample, 0 for u8 and
+                    // (0 - mean[c]) / std[c] = bias[c] for f32 (bias[0] for gray): the quad store of
+                    // zero interpolants
+                    QuadOut<OUTK> Z;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        Z.u[j].r = Z.u[j].g = Z.u[j].b = 0u;
+                        Z.f[j][0] = Z.f[j][1] = Z.f[j][2] = 0.f;
+                    }
+                    quad_store<OUTK>(Z, J, chw, row_off(hr, 0), chw ? row_off(hr, 1) : 0u, chw ? row_off(hr, 2) : 0u, cb);
                 } else {
                     // per-pixel paths: columns l16 + 16 j of row r
                     const ORow o = orow_of(hr);
                     const int y = ty0 + r;
-                    if (mode == PM_ZERO) {
-                        // every tap lies outside the image: the zero sample, 0 for u8 and
-                        // (0 - mean[c]) / std[c] = bias[c] for f32 (bias[0] for gray)
-#pragma unroll
-                        for (int j = 0; j < TW / 16; ++j) {
-                            const int c = l16 + 16 * j;
-                            if (c >= nx) continue;
-                            if (!OT::is_f32) {
-#pragma unroll
-                                for (int q = 0; q < dC; ++q) o.p0[c * dC + q] = 0;
-                            } else if (chw) {
-                                reinterpret_cast<float *>(o.p0)[c] = J.bias[0];
-                                reinterpret_cast<float *>(o.p1)[c] = J.bias[1];
-                                reinterpret_cast<float *>(o.p2)[c] = J.bias[2];
-                            } else {
-#pragma unroll
-                                for (int q = 0; q < dC; ++q) reinterpret_cast<float *>(o.p0)[c * dC + q] = J.bias[q];
-                            }
-                        }
-                    } else if (mode == PM_STAGED && (fast || OP == OP_RESIZE)) {
-                        // staged, part of the tile outside the image's last tile column: the
-                        // definition's taps from the raw rows (resize: the tables)
-                        constexpr int F = TAPS_RAW;
-#pragma unroll
-                        for (int j = 0; j < TW / 16; ++j) {
-                            const int c = l16 + 16 * j;
-                            if (c >= nx) continue;
-                            int x0, y0, qx, qy, dy = 1;
-                            float fx = 0.f, fy = 0.f;
-                            if (OP == OP_RESIZE) {
-                                x0 = sl.cx0[c]; qx = sl.cqd[c] & 0xFFFF; fx = sl.cf[c];
-                                y0 = sl.ry0[r]; qy = sl.rqd[r] & 0xFFFF; dy = sl.rqd[r] >> 16; fy = sl.rf[r];
-                            } else {
-                                float sx, sy;
-                                map_coord<OP>(J.M, tx0 + c, y, sx, sy);   // valid: the tile's corners are
-                                warp_weight(sx, x0, qx);
-                                warp_weight(sy, y0, qy);
-                                if (OT::is_f32) {
-                                    fx = __fsub_rn(sx, floorf(sx));
-                                    fy = __fsub_rn(sy, floorf(sy));
-                                }
-                            }
-                            // the pair (x0, x0 + 1) even where x1 = x0 (resize right edge: q = 0)
-                            const int off = (y0 - fy0) * rstride + 3 * (x0 - fx0) + rph;
-                            const uint8_t *wp = raw + (off & ~3);
-                            const uint32_t sh8 = (uint32_t)off << 3;
-                            uint32_t p00, p01, p10, p11;
-                            raw_pair(wp, sh8, p00, p01);
-                            raw_pair(wp + dy * rstride, sh8, p10, p11);
-                            emit<CIN, OUTK, F>(J, o, c, p00, p01, p10, p11, qx, qy, fx, fy);
-                        }
-                    } else if (OP != OP_RESIZE && mode == PM_STAGED && clamp) {
+                    if (OP != OP_RESIZE && mode == PM_STAGED && clamp) {
                         // replicated border, footprint crossing the image's edge: the box is the
                         // footprint clipped to the image; each tap is clamped into the image
                         const int bx = J.W - 1 - fx0, by = J.H - 1 - fy0;   // box-relative image edges

@@ -169,15 +169,18 @@ struct QuadTile {
 };
 
 // Set-up of the quad state: cx0/cqd/cf are the resize column tables of the tile (shared
-// memory), sraw the offset of the staged box, rph the phase of its rows.
+// memory), sraw the offset of the staged box, rph the phase of its rows. Columns at or past nx
+// (a tile at the image's right edge) repeat column nx - 1: their taps stay inside the box, and
+// the values they produce land in stage columns that are never written out.
 template <int OP, int OUTK>
 __device__ __forceinline__ void quad_setup(QuadTile &T, const Job &J, const int *cx0, const int *cqd, const float *cf,
-                                           int tx0, int fx0, int fy0, int rstride, uint32_t sraw, int rph, int cb)
+                                           int tx0, int fx0, int fy0, int rstride, uint32_t sraw, int rph, int cb,
+                                           int nx)
 {
     if (OP == OP_RESIZE) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int c = cb + j;
+            const int c = min(cb + j, nx - 1);
             T.xo[j] = sraw + (uint32_t)(rph + 3 * (cx0[c] - fx0));
             T.wq[j] = wpair(cqd[c] & 0xFFFF);
             T.fxs[j] = cf[c];
@@ -185,7 +188,7 @@ __device__ __forceinline__ void quad_setup(QuadTile &T, const Job &J, const int 
     } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const float xc = __fadd_rn((float)(tx0 + cb + j), 0.5f);
+            const float xc = __fadd_rn((float)(tx0 + min(cb + j, nx - 1)), 0.5f);
             T.xc2[j] = f2_pack(xc, xc);
         }
         T.mx = f2_pack(J.M[0], J.M[3]);

@@ -368,7 +368,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                 const uint32_t sraw = (uint32_t)(raw - smem);
                 const uint32_t sost = (uint32_t)(ostage - smem);
                 QuadTile T;
-                quad_setup<OP, OUTK>(T, J, ts.cx0, ts.cqd, ts.cf, tx0, fx0, fy0, rstride, sraw, rph, cb);
+                quad_setup<OP, OUTK>(T, J, ts.cx0, ts.cqd, ts.cf, tx0, fx0, fy0, rstride, sraw, rph, cb, nx);
                 for (int rr = 2 * warp + half; rr < BH; rr += 2 * kWarps) {
                     const int r = r0 + rr;
                     if (r >= r1) break;
