@@ -13,9 +13,13 @@
 
 namespace kr {
 
-// Tile shape of the per-operation kernels.
+// Tile shape of the per-operation kernels: 64 columns (the 4-pixel quad path), and a height
+// per kind.
 constexpr int kTW = 64;
-constexpr int kTH = 32;
+template <int OP, int OUTK> constexpr int op_tile_h()
+{
+    return OUTK == OUT_U8_GRAY ? 64 : (OUTK == OUT_F32 || OUTK == OUT_F32_GRAY) ? (OP == OP_RESIZE ? 32 : 32) : (OP == OP_RESIZE ? 32 : 32);
+}
 
 // Device error flags of the per-operation kernels (bit 0: a bounded TMA wait ran out).
 static __device__ unsigned g_kr_device_err;
@@ -263,7 +267,7 @@ static bool encode_map(CUtensorMap *m, const void *base, int64_t rowbytes, int r
 template <int OP, int CIN, int OUTK>
 static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
 {
-    constexpr int TW = kTW, TH = kTH;
+    constexpr int TW = kTW, TH = op_tile_h<OP, OUTK>();
     auto kern_map = resample_kernel<OP, CIN, OUTK, TW, TH, false>;
     auto kern_rows = resample_kernel<OP, CIN, OUTK, TW, TH, CIN == 3>;
     constexpr int ob = out_stage_bytes<OUTK, CIN, TW, TH>();
@@ -271,7 +275,7 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 32 || !(attr_done & (1u << dev))) {
-        const int max_smem = kFootCap + std::max(kRegionBCap, out_stage_bytes<OUTK, CIN, TW, TH>());
+        const int max_smem = std::max(kFootCap, (int)kRawBoxCap + 128) + std::max(kRegionBCap, ob);
         cudaError_t e = cudaFuncSetAttribute(kern_map, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(kern_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);

@@ -53,6 +53,23 @@ __device__ __forceinline__ TileDec decide_staging(const Job &J, const TileShared
     return d;
 }
 
+// One tile per CTA: the thread that planned the box takes the staging decision at once and, when
+// the box is one TMA copy, initialises the staging barrier and starts the copy, so that the copy
+// runs while the other threads finish the plan (the box's origin and size are the same values
+// every thread later decides on).
+template <int OP, int CIN, bool ROWS, int TW, int TH>
+__device__ __forceinline__ void early_tma(const Job &J, TileShared<TW, TH> &ts, uint8_t *smem)
+{
+    const TileDec d = decide_staging<OP, CIN, ROWS, true>(J, ts);
+    if (!(d.flags & TD_TMA)) return;
+    uint8_t *raw = (CIN == 3 && !(d.flags & TD_RAWBOX)) ? smem + J.foot_budget : smem;
+    mbar_init(&ts.mbar);
+    ts.mbar_phase = 0;
+    ts.mbar_ok = 1;
+    mbar_expect_tx(&ts.mbar, (uint32_t)(16 * J.tin_nc * J.tin_br));
+    tma_load_3d(raw, J.tin, 4 * ((ts.ti.fx0 * CIN) >> 4), ts.ti.fy0, J.zimg, &ts.mbar);
+}
+
 // ROWS: the bulk row-copy staging is compiled in. FRESH: the CTA runs this one tile, and the
 // staging barrier is initialised right before its copies; otherwise the caller ran
 // tile_shared_init once and the barrier's phase carries over from tile to tile.
@@ -71,8 +88,11 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     const int nx = min(TW, J.w - tx0), ny = min(TH, J.h - ty0);
 
     // ---- 1. plan -----------------------------------------------------------------
+    // The thread that starts a one-tile CTA's box copy early (after planning the box itself).
+    constexpr int kIssuer = (FRESH && OP == OP_RESIZE) ? TW + TH : 0;
     if (OP == OP_RESIZE) {
-        static_assert(TW + TH <= kThreads, "one axis entry per thread");
+        static_assert(TW + TH <= kThreads && (!FRESH || (TW + TH < kThreads && (TW + TH) % 32 == 0)),
+                      "one axis entry per thread (and a spare warp for one-tile CTAs)");
         if (tid < TW) {
             int i0 = 0, i1 = 0, q = 0;
             float f = 0.f;
@@ -90,13 +110,36 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                 else resize_axis(ty0 + r, J.H, J.h, i0, i1, q, f);
             }
             ts.ry0[r] = i0; ts.rqd[r] = q | ((i1 - i0) << 16); ts.rf[r] = f;
+        } else if (FRESH && warp == kIssuer / 32) {
+            // the box from the first and last column and row of the tile (their taps are the
+            // tables' first and last entries; lanes 0..3 take one each), then its copy
+            const bool col = lane < 2;
+            const int i = col ? tx0 + (lane & 1) * (nx - 1) : ty0 + (lane & 1) * (ny - 1);
+            int i0 = 0, i1 = 0, q = 0;
+            float f = 0.f;
+            if (lane < 4) {
+                const int n_in = col ? J.W : J.H, n_out = col ? J.w : J.h;
+                if (J.rm[0]) resize_axis_m(i, n_in, n_out, J.rm[col ? 0 : 2], J.rm[col ? 1 : 3], i0, i1, q, f);
+                else resize_axis(i, n_in, n_out, i0, i1, q, f);
+            }
+            const int b0 = __shfl_sync(0xffffffffu, i0, 0), b1 = __shfl_sync(0xffffffffu, i1, 1);
+            const int b2 = __shfl_sync(0xffffffffu, i0, 2), b3 = __shfl_sync(0xffffffffu, i1, 3);
+            if (lane == 0) {
+                ti.fx0 = b0;
+                ti.fx1 = b1;
+                ti.fy0 = b2;
+                ti.fy1 = b3;
+                early_tma<OP, CIN, ROWS>(J, ts, smem);
+            }
         }
-        __syncthreads();
-        if (tid == 0) {
-            ti.fx0 = ts.cx0[0];
-            ti.fx1 = ts.cx0[nx - 1] + (ts.cqd[nx - 1] >> 16);
-            ti.fy0 = ts.ry0[0];
-            ti.fy1 = ts.ry0[ny - 1] + (ts.rqd[ny - 1] >> 16);
+        if (!FRESH) {
+            __syncthreads();
+            if (tid == 0) {
+                ti.fx0 = ts.cx0[0];
+                ti.fx1 = ts.cx0[nx - 1] + (ts.cqd[nx - 1] >> 16);
+                ti.fy0 = ts.ry0[0];
+                ti.fy1 = ts.ry0[ny - 1] + (ts.rqd[ny - 1] >> 16);
+            }
         }
     } else if (warp == 0) {
         // Lanes 0..3 map one tile corner each; the box is their hull, one pixel wider
@@ -141,6 +184,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             ti.fast = fast;
             ti.zero = zero;
             ti.clamp = clamp;
+            if (FRESH) early_tma<OP, CIN, ROWS>(J, ts, smem);
         }
     }
     __syncthreads();
@@ -176,10 +220,11 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             // of each row (rows are 16-byte aligned, so every row has the same phase). Words
             // outside the image (left of it, right of its last word, above, below) arrive as
             // zeros: the zero border of warp boxes.
-            if (tid == 0) {
-                if (FRESH) tile_shared_init(ts);
-                mbar_expect_tx(&ts.mbar, (uint32_t)(16 * J.tin_nc * J.tin_br));
-                tma_load_3d(raw, J.tin, 4 * ((fx0 * CIN) >> 4), fy0, J.zimg, &ts.mbar);
+            if (tid == kIssuer) {
+                if (!FRESH) {   // (one tile per CTA: started right after the plan)
+                    mbar_expect_tx(&ts.mbar, (uint32_t)(16 * J.tin_nc * J.tin_br));
+                    tma_load_3d(raw, J.tin, 4 * ((fx0 * CIN) >> 4), fy0, J.zimg, &ts.mbar);
+                }
                 stage_wait(ts, J.err, J.wait_ns);
             }
             __syncthreads();
