@@ -201,15 +201,49 @@ __device__ __forceinline__ void quad_setup(QuadTile &T, const Job &J, const int 
     }
 }
 
-// One row r of the lane's quad: blend and store at off0 (planar f32: plane rows off0, off1,
-// off2). ry0/rqd/rf are the resize row tables.
+// Store a lane's 4 adjacent f32 output pixels straight to global memory: g0 = the pixels' row
+// (planar: plane 0's row; planes oplane bytes apart), 16-byte aligned, as is every 4-pixel
+// group of it (16-byte stores).
+template <int OUTK>
+__device__ __forceinline__ void quad_store_global(const QuadOut<OUTK> &Q, const Job &J, bool chw, uint8_t *g0,
+                                                  int64_t oplane, int cb)
+{
+    if constexpr (OUTK == OUT_F32_GRAY) {
+        float g[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float v = __fmaf_rn(0.299f, Q.f[j][0], __fmaf_rn(0.587f, Q.f[j][1], __fmul_rn(0.114f, Q.f[j][2])));
+            g[j] = __fmaf_rn(v, J.scale[0], J.bias[0]);
+        }
+        *reinterpret_cast<float4 *>(g0 + 4 * cb) = make_float4(g[0], g[1], g[2], g[3]);
+    } else if constexpr (OUTK == OUT_F32) {
+        if (chw) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                *reinterpret_cast<float4 *>(g0 + k * oplane + 4 * cb) =
+                    make_float4(__fmaf_rn(Q.f[0][k], J.scale[k], J.bias[k]), __fmaf_rn(Q.f[1][k], J.scale[k], J.bias[k]),
+                                __fmaf_rn(Q.f[2][k], J.scale[k], J.bias[k]), __fmaf_rn(Q.f[3][k], J.scale[k], J.bias[k]));
+        } else {
+            float w[12];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) w[3 * j + k] = __fmaf_rn(Q.f[j][k], J.scale[k], J.bias[k]);
+            float4 *d = reinterpret_cast<float4 *>(g0 + 12 * cb);
+            d[0] = make_float4(w[0], w[1], w[2], w[3]);
+            d[1] = make_float4(w[4], w[5], w[6], w[7]);
+            d[2] = make_float4(w[8], w[9], w[10], w[11]);
+        }
+    }
+}
+
+// One row r of the lane's quad: the blended values of its 4 pixels. ry0/rqd/rf are the resize
+// row tables.
 template <int OP, int OUTK>
-__device__ __forceinline__ void quad_row(const QuadTile &T, const Job &J, const int *ry0, const int *rqd,
-                                         const float *rf, int r, int ty0, int fy0, int rstride, uint32_t sraw,
-                                         bool chw, uint32_t off0, uint32_t off1, uint32_t off2, int cb)
+__device__ __forceinline__ void quad_eval(QuadOut<OUTK> &Q, const QuadTile &T, const Job &J, const int *ry0,
+                                          const int *rqd, const float *rf, int r, int ty0, int fy0, int rstride)
 {
     using OT = OutTraits<OUTK, 3>;
-    QuadOut<OUTK> Q;
     if (OP == OP_RESIZE) {
         const int rq = rqd[r];
         const uint32_t wy1 = (uint32_t)(rq & 0xFFFF) << 2;
@@ -260,6 +294,17 @@ __device__ __forceinline__ void quad_row(const QuadTile &T, const Job &J, const 
             quad_blend<OUTK>(Q, j, p00, p01, p10, p11, wx, wy1, fx, fy);
         }
     }
+}
+
+// One row r of the lane's quad: blend and store into the output stage at off0 (planar f32:
+// plane rows off0, off1, off2).
+template <int OP, int OUTK>
+__device__ __forceinline__ void quad_row(const QuadTile &T, const Job &J, const int *ry0, const int *rqd,
+                                         const float *rf, int r, int ty0, int fy0, int rstride, uint32_t sraw,
+                                         bool chw, uint32_t off0, uint32_t off1, uint32_t off2, int cb)
+{
+    QuadOut<OUTK> Q;
+    quad_eval<OP, OUTK>(Q, T, J, ry0, rqd, rf, r, ty0, fy0, rstride);
     quad_store<OUTK>(Q, J, chw, off0, off1, off2, cb);
 }
 

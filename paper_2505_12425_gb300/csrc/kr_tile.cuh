@@ -377,6 +377,25 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
         return o;
     };
 
+    const bool quad = CIN == 3 && TW == 64 && fast && rawbox && nx == TW;
+    if constexpr (OT::is_f32 && CIN == 3 && TW == 64) {
+        if (quad && tma_out) {
+            // f32 rows that are whole 16-byte chunks: each lane stores its 4 pixels straight to
+            // global memory (16-byte stores), all rows of the tile in one pass, with no output
+            // stage and no barrier after the staging one
+            const int half = lane >> 4, cb = 4 * (lane & 15);
+            const uint32_t sraw = (uint32_t)(raw - smem);
+            QuadTile T;
+            quad_setup<OP, OUTK>(T, J, ts.cx0, ts.cqd, ts.cf, tx0, fx0, fy0, rstride, sraw, rph, cb, nx);
+            uint8_t *g = J.dst + (int64_t)ty0 * J.dpitch + (chw ? (int64_t)tx0 * 4 : (int64_t)tx0 * dC * ES);
+            for (int r = 2 * warp + half; r < ny; r += 2 * kWarps) {
+                QuadOut<OUTK> Q;
+                quad_eval<OP, OUTK>(Q, T, J, ts.ry0, ts.rqd, ts.rf, r, ty0, fy0, rstride);
+                quad_store_global<OUTK>(Q, J, chw, g + (int64_t)r * J.dpitch, J.dplane, cb);
+            }
+            return;
+        }
+    }
     for (int band = 0; band < NBAND; ++band) {
         r0 = band * BH;
         if (r0 >= ny) break;
@@ -405,7 +424,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                     }
                 }
             }
-        } else if (CIN == 3 && TW == 64 && fast && rawbox && nx == TW) {
+        } else if (quad) {
             // Full-width tile with raw taps: each lane blends 4 adjacent pixels of a row (half-
             // warps on neighbouring rows) and stores them as packed words.
             if constexpr (CIN == 3 && TW == 64) {
