@@ -18,7 +18,7 @@ namespace kr {
 constexpr int kTW = 64;
 template <int OP, int OUTK> constexpr int op_tile_h()
 {
-    return OUTK == OUT_U8_GRAY ? 64 : (OUTK == OUT_F32 || OUTK == OUT_F32_GRAY) ? (OP == OP_RESIZE ? 32 : 32) : (OP == OP_RESIZE ? 32 : 32);
+    return OUTK == OUT_U8_GRAY ? 64 : (OUTK == OUT_F32 || OUTK == OUT_F32_GRAY) ? (OP == OP_RESIZE ? 32 : 32) : (OP == OP_RESIZE ? 64 : 32);
 }
 
 // Device error flags of the per-operation kernels (bit 0: a bounded TMA wait ran out).

@@ -201,14 +201,30 @@ __device__ __forceinline__ void quad_setup(QuadTile &T, const Job &J, const int 
     }
 }
 
-// Store a lane's 4 adjacent f32 output pixels straight to global memory: g0 = the pixels' row
-// (planar: plane 0's row; planes oplane bytes apart), 16-byte aligned, as is every 4-pixel
-// group of it (16-byte stores).
+// Store a lane's 4 adjacent output pixels straight to global memory: g0 = the pixels' row
+// (planar: plane 0's row; planes oplane bytes apart), 16-byte aligned (f32: 16-byte stores of
+// each 4-pixel group; u8: 4-byte stores).
 template <int OUTK>
 __device__ __forceinline__ void quad_store_global(const QuadOut<OUTK> &Q, const Job &J, bool chw, uint8_t *g0,
                                                   int64_t oplane, int cb)
 {
-    if constexpr (OUTK == OUT_F32_GRAY) {
+    if constexpr (OUTK == OUT_U8) {
+        const uint32_t a0 = __byte_perm(Q.u[0].r, Q.u[0].g, 0x0073), a1 = __byte_perm(Q.u[0].b, Q.u[1].r, 0x0073);
+        const uint32_t b0 = __byte_perm(Q.u[1].g, Q.u[1].b, 0x0073), b1 = __byte_perm(Q.u[2].r, Q.u[2].g, 0x0073);
+        const uint32_t c0 = __byte_perm(Q.u[2].b, Q.u[3].r, 0x0073), c1 = __byte_perm(Q.u[3].g, Q.u[3].b, 0x0073);
+        uint32_t *d = reinterpret_cast<uint32_t *>(g0 + 3 * cb);
+        d[0] = __byte_perm(a0, a1, 0x5410);
+        d[1] = __byte_perm(b0, b1, 0x5410);
+        d[2] = __byte_perm(c0, c1, 0x5410);
+    } else if constexpr (OUTK == OUT_U8_GRAY) {
+        uint32_t g[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            g[j] = __dp2a_lo(4899u | (9617u << 16), __byte_perm(Q.u[j].r, Q.u[j].g, 0x0073),
+                             8192u + 1868u * (Q.u[j].b >> 24)) >> 14;
+        *reinterpret_cast<uint32_t *>(g0 + cb) =
+            __byte_perm(__byte_perm(g[0], g[1], 0x0040), __byte_perm(g[2], g[3], 0x0040), 0x5410);
+    } else if constexpr (OUTK == OUT_F32_GRAY) {
         float g[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {

@@ -378,11 +378,11 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     };
 
     const bool quad = CIN == 3 && TW == 64 && fast && rawbox && nx == TW;
-    if constexpr (OT::is_f32 && CIN == 3 && TW == 64) {
+    if constexpr (CIN == 3 && TW == 64) {
         if (quad && tma_out) {
-            // f32 rows that are whole 16-byte chunks: each lane stores its 4 pixels straight to
-            // global memory (16-byte stores), all rows of the tile in one pass, with no output
-            // stage and no barrier after the staging one
+            // rows that are whole 16-byte chunks: each lane stores its 4 pixels straight to
+            // global memory, all rows of the tile in one pass, with no output stage and no
+            // barrier after the staging one
             const int half = lane >> 4, cb = 4 * (lane & 15);
             const uint32_t sraw = (uint32_t)(raw - smem);
             QuadTile T;
