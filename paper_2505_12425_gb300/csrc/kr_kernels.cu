@@ -13,13 +13,11 @@
 
 namespace kr {
 
-// Tile shape of the per-operation kernels: 64 columns (the 4-pixel quad path), and a height
-// per kind.
+// Tile shape of the per-operation kernels: 64 columns (the 4-pixel quad path) by 64 rows for
+// every kind (measured against 32 rows: with no output stage, taller tiles halve the per-tile
+// work of planning and staging at the same residency).
 constexpr int kTW = 64;
-template <int OP, int OUTK> constexpr int op_tile_h()
-{
-    return OUTK == OUT_U8_GRAY ? 64 : (OUTK == OUT_F32 || OUTK == OUT_F32_GRAY) ? (OP == OP_RESIZE ? 32 : 32) : (OP == OP_RESIZE ? 64 : 32);
-}
+template <int OP, int OUTK> constexpr int op_tile_h() { return 64; }
 
 // Device error flags of the per-operation kernels (bit 0: a bounded TMA wait ran out).
 static __device__ unsigned g_kr_device_err;
@@ -392,6 +390,12 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
             p.has_tout = encode_map(&p.tout, p.dst, orowb, d.h, chw ? 3 : 1, nb, d.dpitch, d.dplane, d.dbatch,
                                     tile_chunks, out_band_rows<OUTK, CIN, TH>()) ? 1 : 0;
         }
+        // Rows that are whole 16-byte chunks are written straight to global memory (no output
+        // stage); region B then only served 3-channel boxes re-laid from raw rows, which launches
+        // with raw taps stage by TMA or bulk copies instead (the perspective warp keeps it for its
+        // most magnified tiles).
+        if (p.has_tout && OP != OP_PERSP && (CIN == 1 || p.raw_taps)) bud.b = 0;
+        p.region_b = bud.b;
         const size_t smem = (size_t)bud.a + bud.b;
         dim3 grid(tiles_x, tiles_y, nb);
         if (p.raw_taps && !p.has_tin)

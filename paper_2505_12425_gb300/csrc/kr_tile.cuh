@@ -362,9 +362,19 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     const uint32_t obase = (uint32_t)(uintptr_t)(J.dst + (int64_t)ty0 * J.dpitch +
                                                  (chw ? (int64_t)tx0 * 4 : (int64_t)tx0 * dC * ES));
     const uint32_t opitch = (uint32_t)J.dpitch, oplane = (uint32_t)J.dplane;
+    // Rows that are whole 16-byte chunks are written straight to global memory by every path
+    // (the quad path with 4- or 16-byte stores, the others pixel by pixel): no output stage.
+    const bool direct = tma_out;
     int r0 = 0;   // first tile row of the current band
     auto orow_of = [&](int r) -> ORow {
         ORow o;
+        if (direct) {
+            uint8_t *g = J.dst + (int64_t)(ty0 + r) * J.dpitch + (chw ? (int64_t)tx0 * 4 : (int64_t)tx0 * dC * ES);
+            o.p0 = g;
+            o.p1 = chw ? g + J.dplane : nullptr;
+            o.p2 = chw ? g + 2 * J.dplane : nullptr;
+            return o;
+        }
         const uint32_t a = obase + (uint32_t)r * opitch;
         const int sr = r - r0;
         o.p0 = ostage + sr * orow + (a & 15u);
@@ -379,10 +389,9 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
 
     const bool quad = CIN == 3 && TW == 64 && fast && rawbox && nx == TW;
     if constexpr (CIN == 3 && TW == 64) {
-        if (quad && tma_out) {
-            // rows that are whole 16-byte chunks: each lane stores its 4 pixels straight to
-            // global memory, all rows of the tile in one pass, with no output stage and no
-            // barrier after the staging one
+        if (quad && direct) {
+            // each lane stores its 4 pixels straight to global memory, all rows of the tile in
+            // one pass, with no barrier after the staging one
             const int half = lane >> 4, cb = 4 * (lane & 15);
             const uint32_t sraw = (uint32_t)(raw - smem);
             QuadTile T;
@@ -396,10 +405,10 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             return;
         }
     }
-    for (int band = 0; band < NBAND; ++band) {
+    for (int band = 0; band < (direct ? 1 : NBAND); ++band) {
         r0 = band * BH;
         if (r0 >= ny) break;
-        const int r1 = min(ny, r0 + BH);
+        const int r1 = direct ? ny : min(ny, r0 + BH);
         if (band > 0) __syncthreads();   // the previous band has left the output stage
 
         if (zero_tile) {
@@ -724,6 +733,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
                 }
             }
         }
+        if (direct) return;   // (written straight to global memory)
         if (tma_out) fence_proxy_async_smem();
         __syncthreads();
 
