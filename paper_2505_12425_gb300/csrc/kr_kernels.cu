@@ -14,10 +14,11 @@
 namespace kr {
 
 // Tile shape of the per-operation kernels: 64 columns (the 4-pixel quad path) by 64 rows for
-// every kind (measured against 32 rows: with no output stage, taller tiles halve the per-tile
-// work of planning and staging at the same residency).
+// resize and 48 for the warps (measured against 32, 48, 64 and 128 rows: with no output stage,
+// taller tiles share the per-tile work of planning and staging among more pixels; the warps'
+// boxes, larger for the same tile, keep 8 CTAs per SM at 48 rows).
 constexpr int kTW = 64;
-template <int OP, int OUTK> constexpr int op_tile_h() { return 64; }
+template <int OP, int OUTK> constexpr int op_tile_h() { return OP == OP_RESIZE ? 64 : 48; }
 
 // Device error flags of the per-operation kernels (bit 0: a bounded TMA wait ran out).
 static __device__ unsigned g_kr_device_err;

@@ -89,9 +89,9 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
 
     // ---- 1. plan -----------------------------------------------------------------
     // The thread that starts a one-tile CTA's box copy early (after planning the box itself).
-    constexpr int kIssuer = (FRESH && OP == OP_RESIZE) ? TW + TH : 0;
+    constexpr int kIssuer = (FRESH && OP == OP_RESIZE) ? (TW + TH + 31) / 32 * 32 : 0;
     if (OP == OP_RESIZE) {
-        static_assert(TW + TH <= kThreads && (!FRESH || (TW + TH < kThreads && (TW + TH) % 32 == 0)),
+        static_assert(TW + TH <= kThreads && (!FRESH || kIssuer + 32 <= kThreads),
                       "one axis entry per thread (and a spare warp for one-tile CTAs)");
         if (tid < TW) {
             int i0 = 0, i1 = 0, q = 0;
