@@ -483,7 +483,33 @@ __device__ __forceinline__ void pipe_consume(Pol &P, PipeShared<TW, TH, NS> &sh,
         QuadTile T;
         if (quad) quad_setup<OP, OUTK>(T, J, sl.cx0, sl.cqd, sl.cf, tx0, fx0, fy0, rstride, sraw, rph, cb, nx);
 
-        for (int ra = UR * warp; ra < ny; ra += UR * NWARP) {
+        // u8 rows of quad and zero tiles go straight to global memory (aligned 4-byte stores
+        // built across each half-warp, any row alignment): no unit stage, no write-out
+        constexpr bool kRunKind = OUTK == OUT_U8 || OUTK == OUT_U8_GRAY;
+        const bool run = kRunKind && (quad || mode == PM_ZERO);
+        if constexpr (kRunKind) {
+            if (run) {
+                constexpr int NW = QuadWords<OUTK>::n;
+                for (int ra = UR * warp; ra < ny; ra += UR * NWARP) {
+#pragma unroll 1
+                    for (int hr = half; hr < UR; hr += 2) {
+                        const int r = ra + hr;
+                        const bool live = r < ny;
+                        uint32_t w[NW];
+#pragma unroll
+                        for (int i = 0; i < NW; ++i) w[i] = 0u;
+                        if (live && quad) {
+                            QuadOut<OUTK> Q;
+                            quad_eval<OP, OUTK>(Q, T, J, sl.ry0, sl.rqd, sl.rf, r, ty0, fy0, rstride);
+                            quad_pack_u8<OUTK>(Q, w);
+                        }
+                        uint8_t *g = live ? J.dst + (int64_t)(ty0 + r) * J.dpitch + (int64_t)tx0 * dC : J.dst;
+                        store_run_u8<NW>(g, live ? nx * dC : 0, w, l16);
+                    }
+                }
+            }
+        }
+        for (int ra = UR * warp; ra < (run ? 0 : ny); ra += UR * NWARP) {
             const uint32_t ub = wbuf + (uint32_t)((u & 1) * unit_bytes);
             // byte offset of (tile row ra + h, plane pl) in the unit stage: dense rows for a TMA
             // store, else keeping the 16-byte phase of the row in global memory

@@ -201,6 +201,60 @@ __device__ __forceinline__ void quad_setup(QuadTile &T, const Job &J, const int 
     }
 }
 
+// The packed bytes of a lane's 4 adjacent u8 output pixels: 12 (3 words) for RGB, 4 for gray.
+template <int OUTK> struct QuadWords {
+    static constexpr int n = OUTK == OUT_U8 ? 3 : 1;
+};
+template <int OUTK>
+__device__ __forceinline__ void quad_pack_u8(const QuadOut<OUTK> &Q, uint32_t (&w)[QuadWords<OUTK>::n])
+{
+    if constexpr (OUTK == OUT_U8) {
+        const uint32_t a0 = __byte_perm(Q.u[0].r, Q.u[0].g, 0x0073), a1 = __byte_perm(Q.u[0].b, Q.u[1].r, 0x0073);
+        const uint32_t b0 = __byte_perm(Q.u[1].g, Q.u[1].b, 0x0073), b1 = __byte_perm(Q.u[2].r, Q.u[2].g, 0x0073);
+        const uint32_t c0 = __byte_perm(Q.u[2].b, Q.u[3].r, 0x0073), c1 = __byte_perm(Q.u[3].g, Q.u[3].b, 0x0073);
+        w[0] = __byte_perm(a0, a1, 0x5410);
+        w[1] = __byte_perm(b0, b1, 0x5410);
+        w[2] = __byte_perm(c0, c1, 0x5410);
+    } else if constexpr (OUTK == OUT_U8_GRAY) {
+        uint32_t g[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            g[j] = __dp2a_lo(4899u | (9617u << 16), __byte_perm(Q.u[j].r, Q.u[j].g, 0x0073),
+                             8192u + 1868u * (Q.u[j].b >> 24)) >> 14;
+        w[0] = __byte_perm(__byte_perm(g[0], g[1], 0x0040), __byte_perm(g[2], g[3], 0x0040), 0x5410);
+    }
+}
+
+// A run of L bytes at g (any alignment) held by the 16 lanes of a half-warp, NW words each
+// (lane l16 holds bytes [4 NW l16, 4 NW (l16 + 1))), written with aligned 4-byte stores: the
+// aligned word k of the run's span (bytes [4k - p, 4k - p + 4) of the run, p = g mod 4) is
+// built from the two words that hold its bytes (the first from the lane below, by a shuffle)
+// and stored by the lane that holds its last bytes; a word the run covers only in part (its
+// first and last) goes byte by byte. Every lane of the warp calls this (L = 0: no stores).
+template <int NW>
+__device__ __forceinline__ void store_run_u8(uint8_t *g, int L, const uint32_t (&x)[NW], int l16)
+{
+    const uint32_t p = (uint32_t)(uintptr_t)g & 3u;
+    uint32_t *A = reinterpret_cast<uint32_t *>(g - p);
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, x[NW - 1], 1, 16);
+    const uint32_t sh = 32u - 8u * p;   // (p = 0: the clamped shift gives the upper word)
+#pragma unroll
+    for (int i = 0; i <= NW; ++i) {
+        if (i == NW && l16 != 15) break;   // (the next lane's first word)
+        const uint32_t lo = i == 0 ? prev : x[i - 1], hi = i < NW ? x[i] : 0u;
+        const uint32_t v = __funnelshift_rc(lo, hi, sh);
+        const int k = NW * l16 + i;
+        const int s0 = 4 * k - (int)p;   // run byte of the word's first byte
+        if (s0 >= 0 && s0 + 4 <= L) {
+            A[k] = v;
+        } else {
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (s0 + b >= 0 && s0 + b < L) g[s0 + b] = (uint8_t)(v >> (8 * b));
+        }
+    }
+}
+
 // Store a lane's 4 adjacent output pixels straight to global memory: g0 = the pixels' row
 // (planar: plane 0's row; planes oplane bytes apart), 16-byte aligned (f32: 16-byte stores of
 // each 4-pixel group; u8: 4-byte stores).
@@ -209,21 +263,16 @@ __device__ __forceinline__ void quad_store_global(const QuadOut<OUTK> &Q, const 
                                                   int64_t oplane, int cb)
 {
     if constexpr (OUTK == OUT_U8) {
-        const uint32_t a0 = __byte_perm(Q.u[0].r, Q.u[0].g, 0x0073), a1 = __byte_perm(Q.u[0].b, Q.u[1].r, 0x0073);
-        const uint32_t b0 = __byte_perm(Q.u[1].g, Q.u[1].b, 0x0073), b1 = __byte_perm(Q.u[2].r, Q.u[2].g, 0x0073);
-        const uint32_t c0 = __byte_perm(Q.u[2].b, Q.u[3].r, 0x0073), c1 = __byte_perm(Q.u[3].g, Q.u[3].b, 0x0073);
+        uint32_t w[3];
+        quad_pack_u8<OUTK>(Q, w);
         uint32_t *d = reinterpret_cast<uint32_t *>(g0 + 3 * cb);
-        d[0] = __byte_perm(a0, a1, 0x5410);
-        d[1] = __byte_perm(b0, b1, 0x5410);
-        d[2] = __byte_perm(c0, c1, 0x5410);
+        d[0] = w[0];
+        d[1] = w[1];
+        d[2] = w[2];
     } else if constexpr (OUTK == OUT_U8_GRAY) {
-        uint32_t g[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            g[j] = __dp2a_lo(4899u | (9617u << 16), __byte_perm(Q.u[j].r, Q.u[j].g, 0x0073),
-                             8192u + 1868u * (Q.u[j].b >> 24)) >> 14;
-        *reinterpret_cast<uint32_t *>(g0 + cb) =
-            __byte_perm(__byte_perm(g[0], g[1], 0x0040), __byte_perm(g[2], g[3], 0x0040), 0x5410);
+        uint32_t w[1];
+        quad_pack_u8<OUTK>(Q, w);
+        *reinterpret_cast<uint32_t *>(g0 + cb) = w[0];
     } else if constexpr (OUTK == OUT_F32_GRAY) {
         float g[4];
 #pragma unroll
