@@ -263,10 +263,10 @@ static bool encode_map(CUtensorMap *m, const void *base, int64_t rowbytes, int r
 // ---------------------------------------------------------------------------
 // Per-operation launch
 // ---------------------------------------------------------------------------
-template <int OP, int CIN, int OUTK>
-static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
+template <int OP, int CIN, int OUTK, int TH>
+static cudaError_t launch_th(const OpDesc &d, cudaStream_t stream)
 {
-    constexpr int TW = kTW, TH = op_tile_h<OP, OUTK>();
+    constexpr int TW = kTW;
     auto kern_map = resample_kernel<OP, CIN, OUTK, TW, TH, false>;
     auto kern_rows = resample_kernel<OP, CIN, OUTK, TW, TH, CIN == 3>;
     constexpr int ob = out_stage_bytes<OUTK, CIN, TW, TH>();
@@ -407,6 +407,25 @@ static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// Tile height of a launch: the kind's height, or 16 rows when the launch has too few tiles to
+// fill the GPU for long (small images): a CTA's time grows with its rows plus a fixed part
+// (planning and staging, about 24 rows' worth), and a launch takes as many of those as it has
+// waves of CTAs (about 8 resident per SM).
+template <int OP, int CIN, int OUTK>
+static cudaError_t launch_t(const OpDesc &d, cudaStream_t stream)
+{
+    constexpr int TB = op_tile_h<OP, OUTK>(), TS = 16;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    const long long tiles_x = (d.w + kTW - 1) / kTW, slots = 8LL * sms;
+    auto cost = [&](int th) {
+        const long long ctas = tiles_x * ((d.h + th - 1) / th) * d.batch;
+        return ((ctas + slots - 1) / slots) * (th + 24);
+    };
+    return cost(TS) < cost(TB) ? launch_th<OP, CIN, OUTK, TS>(d, stream) : launch_th<OP, CIN, OUTK, TB>(d, stream);
 }
 
 template <int OP>
