@@ -92,7 +92,7 @@ static __device__ unsigned long long g_kr_stage_wait_ns = kTmaWaitNs;
 
 // Staging ring depth and tile shape of the pipelined ragged kernels.
 constexpr int kPipeStages = 2;
-constexpr int kPipeTW = 64, kPipeTH = 32;
+constexpr int kPipeTW = 64, kPipeTH = 64;
 
 // Kinds that run on the pipelined engine (3-channel resize and warp).
 constexpr bool pipe_kind(int kind) { return kind != KIND_GRAY && ((kind >> 4) & 15) == 3; }
@@ -319,14 +319,14 @@ template <int TW, int TH> static constexpr int max_region_b()
      (const void *)ragged_kernel<TW, TH, 12>}
 // Configuration 0 (64 x 32 tiles) runs the 3-channel resample kinds on the pipelined kernel.
 static TileCfg g_cfgs[] = {
-    {64, 32,
+    {64, 64,
      {(const void *)ragged_pipe_kernel<0>, (const void *)ragged_pipe_kernel<1>, (const void *)ragged_pipe_kernel<2>,
-      (const void *)ragged_pipe_kernel<3>, (const void *)ragged_kernel<64, 32, 4>,
-      (const void *)ragged_kernel<64, 32, 5>, (const void *)ragged_pipe_kernel<6>,
+      (const void *)ragged_pipe_kernel<3>, (const void *)ragged_kernel<64, 64, 4>,
+      (const void *)ragged_kernel<64, 64, 5>, (const void *)ragged_pipe_kernel<6>,
       (const void *)ragged_pipe_kernel<7>, (const void *)ragged_pipe_kernel<8>, (const void *)ragged_pipe_kernel<9>,
-      (const void *)ragged_kernel<64, 32, 10>, (const void *)ragged_kernel<64, 32, 11>,
-      (const void *)ragged_kernel<64, 32, 12>},
-     kFootCap + max_region_b<64, 32>()},
+      (const void *)ragged_kernel<64, 64, 10>, (const void *)ragged_kernel<64, 64, 11>,
+      (const void *)ragged_kernel<64, 64, 12>},
+     kFootCap + max_region_b<64, 64>()},
     {32, 32, KR_KERNELS(32, 32), kFootCap + max_region_b<32, 32>()},
     {128, 16, KR_KERNELS(128, 16), kFootCap + max_region_b<128, 16>()},
     {64, 16, KR_KERNELS(64, 16), kFootCap + max_region_b<64, 16>()},
