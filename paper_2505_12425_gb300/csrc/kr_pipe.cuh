@@ -408,7 +408,9 @@ template <int OUTK> __host__ __device__ constexpr int pipe_unit_rows()
 // Bytes of one unit stage (UR rows; three planes of UR rows for planar f32), a multiple of 128.
 template <int OUTK, int TW> __host__ __device__ constexpr int pipe_unit_bytes()
 {
-    return (OutTraits<OUTK, 3>::is_f32 && OutTraits<OUTK, 3>::dC == 3)
+    // (u8 rows go straight to global memory: no unit stage)
+    return (OUTK == OUT_U8 || OUTK == OUT_U8_GRAY) ? 0
+           : (OutTraits<OUTK, 3>::is_f32 && OutTraits<OUTK, 3>::dC == 3)
                ? (((pipe_unit_rows<OUTK>() * round16(TW * 12 + 15) > 3 * pipe_unit_rows<OUTK>() * round16(TW * 4 + 15)
                         ? pipe_unit_rows<OUTK>() * round16(TW * 12 + 15)
                         : 3 * pipe_unit_rows<OUTK>() * round16(TW * 4 + 15)) + 127) & ~127)
@@ -519,6 +521,11 @@ __device__ __forceinline__ void pipe_consume(Pol &P, PipeShared<TW, TH, NS> &sh,
             };
             auto orow_of = [&](int h) -> ORow {
                 ORow o;
+                if (kRunKind) {   // u8: straight to the destination row
+                    o.p0 = J.dst + (int64_t)(ty0 + ra + h) * J.dpitch + (int64_t)tx0 * dC;
+                    o.p1 = o.p2 = nullptr;
+                    return o;
+                }
                 o.p0 = kr_pipe_smem + row_off(h, 0);
                 if (chw) {
                     o.p1 = kr_pipe_smem + row_off(h, 1);
@@ -632,6 +639,7 @@ __device__ __forceinline__ void pipe_consume(Pol &P, PipeShared<TW, TH, NS> &sh,
                 }
             }
             }
+            if (kRunKind) continue;   // (written straight to global memory)
             __syncwarp();
 
             // ---- write-out of the unit ----
