@@ -137,7 +137,7 @@ __device__ __forceinline__ Job job_of(const WorkItem &it)
     J.raw_taps = (it.flags & ITEM_RAW) ? 1 : 0;
     J.rows16 = (it.flags & ITEM_ROWS16) ? 1 : 0;
     J.replicate = (it.flags & ITEM_REPLICATE) ? 1 : 0;
-    J.tout = nullptr;
+    J.direct = 0;
     J.zimg = 0;
     J.err = &g_kr_batch_err;
     J.wait_ns = g_kr_stage_wait_ns;

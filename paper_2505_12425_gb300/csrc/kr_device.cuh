@@ -17,9 +17,10 @@
 //      packed one-fma weight forms are exact) run a branch-free pixel loop; other tiles
 //      (coordinates outside that range, boxes too large for shared memory, non-finite or
 //      huge coordinates) take the medium or general per-pixel paths;
-//   4. write-out: results go into a shared copy of the output tile (two bands of rows for
-//      f32) and leave through a TMA store per band, else through 128-bit coalesced stores
-//      (head and tail bytes one per lane).
+//   4. write-out: when the destination rows are whole 16-byte chunks at 16-byte aligned
+//      addresses (Job::direct) the pixels go straight from registers to global memory; else
+//      into a shared copy of the output tile (two bands of rows for f32) that leaves through
+//      128-bit coalesced stores (head and tail bytes one per lane).
 //
 // Arithmetic (definitions shared with the C ABI documentation):
 //   resize   sx = (x + 1/2) W / w - 1/2 as the exact rational num/den, clamp to
@@ -61,11 +62,12 @@ struct Job {
                           // bulk row copies read their taps from the raw rows, not re-laid words
     int32_t rows16;       // source base and pitch are 16-byte aligned (bulk row copies possible)
     int32_t replicate;    // warps: taps outside the image read the nearest edge pixel (else zero)
-    // TMA (per-operation kernels; null in the ragged kernel). Both maps view images as
-    // {32-bit word, row, (plane,) image} tensors whose rows are a whole number of words.
-    const CUtensorMap *tin;   // source map, box {4 tin_nc words, tin_br rows, 1}; null = cp.async staging
+    // TMA source map (per-operation kernels; null in the ragged kernel): the images as
+    // {32-bit word, row, image} tensors whose rows are a whole number of words.
+    const CUtensorMap *tin;   // box {4 tin_nc words, tin_br rows, 1}; null = cp.async staging
     int32_t tin_nc, tin_br;   // box row in 16-byte chunks, box rows
-    const CUtensorMap *tout;  // destination map, box = one output tile; null = 128-bit stores
+    int32_t direct;           // destination rows are whole 16-byte chunks at 16-byte aligned
+                              // addresses: tiles are written straight from registers
     int32_t zimg;             // image coordinate of this job in both maps
     unsigned *err;            // device error flags (bit 0: a bounded TMA wait ran out)
     uint64_t wait_ns;         // bound of the first wait for a staged box (0: give up at once)
@@ -313,27 +315,6 @@ __device__ __forceinline__ void bulk_load(void *sdst, const void *gsrc, uint32_t
                      smem_addr(sdst)),
                  "l"(reinterpret_cast<uint64_t>(gsrc)), "r"(bytes), "r"(smem_addr(mbar))
                  : "memory");
-}
-
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int c0, int c1, int c2, const void *ssrc)
-{
-    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(ssrc))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tma_store_4d(const CUtensorMap *map, int c0, int c1, int c2, int c3, const void *ssrc)
-{
-    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];\n" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(ssrc))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tma_store_commit_and_wait_read()
-{
-    asm volatile("cp.async.bulk.commit_group;\ncp.async.bulk.wait_group.read 0;\n" ::: "memory");
 }
 
 // Make this thread's generic-proxy shared-memory writes visible to the TMA (async proxy).

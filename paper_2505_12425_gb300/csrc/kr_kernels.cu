@@ -32,8 +32,8 @@ constexpr long long kRawBoxCap = 56 * 1024;
 
 struct OpParams {
     CUtensorMap tin;    // source map (valid when has_tin)
-    CUtensorMap tout;   // destination map (valid when has_tout)
-    int32_t has_tin, has_tout;
+    int32_t has_tin;
+    int32_t direct;     // destination rows are whole 16-byte chunks at 16-byte aligned addresses
     int32_t tin_nc, tin_br;
     const uint8_t *src;
     int64_t spitch, sbatch;
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(kThreads, resample_min_ctas<OP, OUTK>()) resam
     J.tin = p.has_tin ? &p.tin : nullptr;
     J.tin_nc = p.tin_nc;
     J.tin_br = p.tin_br;
-    J.tout = p.has_tout ? &p.tout : nullptr;
+    J.direct = p.direct;
     J.zimg = z;
     J.err = &g_kr_device_err;
     J.wait_ns = g_kr_stage_wait_ns;
@@ -381,21 +381,16 @@ static cudaError_t launch_th(const OpDesc &d, cudaStream_t stream)
         }
         p.foot_budget = bud.a;
         p.region_b = bud.b;
-        // TMA destination map: one band of a tile, when every row is a whole number of 16-byte chunks
-        p.has_tout = 0;
+        // Destination rows that are whole 16-byte chunks at 16-byte aligned addresses (every row,
+        // plane and image) are written straight from registers; region B then only served
+        // 3-channel boxes re-laid from raw rows, which launches with raw taps stage by TMA or
+        // bulk copies instead (the perspective warp keeps it for its most magnified tiles).
         constexpr int dC = OutTraits<OUTK, CIN>::dC, ES = OutTraits<OUTK, CIN>::esize;
         const bool chw = d.chw != 0;
         const int64_t orowb = chw ? (int64_t)d.w * 4 : (int64_t)d.w * dC * ES;
-        if (orowb % 16 == 0) {
-            const int tile_chunks = chw ? TW * 4 / 16 : TW * dC * ES / 16;
-            p.has_tout = encode_map(&p.tout, p.dst, orowb, d.h, chw ? 3 : 1, nb, d.dpitch, d.dplane, d.dbatch,
-                                    tile_chunks, out_band_rows<OUTK, CIN, TH>()) ? 1 : 0;
-        }
-        // Rows that are whole 16-byte chunks are written straight to global memory (no output
-        // stage); region B then only served 3-channel boxes re-laid from raw rows, which launches
-        // with raw taps stage by TMA or bulk copies instead (the perspective warp keeps it for its
-        // most magnified tiles).
-        if (p.has_tout && OP != OP_PERSP && (CIN == 1 || p.raw_taps)) bud.b = 0;
+        p.direct = orowb % 16 == 0 && ((uintptr_t)p.dst & 15) == 0 && (d.dpitch & 15) == 0 && d.dpitch >= orowb &&
+                   (!chw || (d.dplane & 15) == 0) && (nb == 1 || (d.dbatch & 15) == 0);
+        if (p.direct && OP != OP_PERSP && (CIN == 1 || p.raw_taps)) bud.b = 0;
         p.region_b = bud.b;
         const size_t smem = (size_t)bud.a + bud.b;
         dim3 grid(tiles_x, tiles_y, nb);

@@ -3,7 +3,7 @@
 // and u8 -> f32 normalisation epilogues of Sec. III (arithmetic as in kr_device.cuh).
 //
 // A CTA holds kPipeConsumers threads (8 warps) that blend tiles and one producer warp that
-// runs ahead of them over the CTA's tiles (a static stride over the launch's tiles):
+// runs ahead of them over the CTA's tiles (claimed from the launch's tile counter):
 //
 //   producer  for tile k: wait until ring slot s = k mod NS is free ("empty" mbarrier, one
 //             arrival per consumer warp), plan the tile into the slot (resize axis tables, or
@@ -13,13 +13,14 @@
 //             the warp: zeros outside the image, the row's last partial 16-byte chunk), then
 //             every lane arrives on the slot's "full" mbarrier (which also completes on the
 //             copies' bytes);
-//   consumers each warp waits on "full" by itself, blends its two-row units of the tile from
-//             the staged raw rows (or, for a tile that is not staged, from global memory)
-//             into its own two unit stages in turn, writes each unit out itself (a TMA store,
-//             or 128-bit stores) and releases the slot when it has read it.
+//   consumers each warp waits on "full" by itself, blends its units of the tile (4 rows for
+//             u8, 2 for f32) from the staged raw rows (or, for a tile that is not staged,
+//             from global memory), writes u8 rows straight to global memory and f32 units
+//             through its own two unit stages in turn (bulk copies of each row's aligned
+//             middle, head and tail bytes by lanes), and releases the slot when it has read it.
 //
-// While tile k is blended the copies of tiles k+1 .. k+NS-1 are in flight, and the TMA
-// store of a unit drains while the warp blends the next: no CTA-wide barrier after set-up.
+// While tile k is blended the copies of tiles k+1 .. k+NS-1 are in flight, and the bulk
+// stores of a unit drain while the warp blends the next: no CTA-wide barrier after set-up.
 // Every wait sleeps on its mbarrier and is bounded: a staging wait that runs out sets error
 // bit 0, waits once more (bounded) for the copies to land and abandons the warp's rows of
 // the tile without writing them; if that also runs out the warp stops.
@@ -395,11 +396,11 @@ __device__ __forceinline__ void pipe_produce(Pol &P, PipeShared<TW, TH, NS> &sh,
 // ---------------------------------------------------------------------------
 // A unit is UR adjacent output rows of a tile, owned by one consumer warp: each half-warp
 // takes every other row of it, its 16 lanes 4 columns each (TW = 64). Warp w takes rows
-// UR w .. UR w + UR - 1, then the rows 8 UR further down. Each warp blends its units into its
-// own two unit stages in turn and writes each unit out itself (a TMA store of its rows, or
-// the warp's 128-bit stores): the consumer warps never wait for one another.
+// UR w .. UR w + UR - 1, then the rows 8 UR further down. Each warp writes its u8 rows straight
+// to global memory, and blends f32 units into its own two unit stages in turn, writing each
+// unit out itself: the consumer warps never wait for one another.
 
-// Rows of a unit: u8 kinds 4 (one unit per warp and 64 x 32 tile), f32 kinds 2.
+// Rows of a unit: u8 kinds 4, f32 kinds 2.
 template <int OUTK> __host__ __device__ constexpr int pipe_unit_rows()
 {
     return OutTraits<OUTK, 3>::is_f32 ? 2 : 4;
@@ -473,8 +474,7 @@ __device__ __forceinline__ void pipe_consume(Pol &P, PipeShared<TW, TH, NS> &sh,
         const uint8_t *raw = kr_pipe_smem + sraw;
         const int rph = (fx0 * 3) & 15;   // phase of every staged row
         const bool chw = OT::is_f32 && dC == 3 && J.chw;
-        const bool tma_out = J.tout != nullptr;
-        const int orow = tma_out ? (chw ? TW * 4 : TW * dC * ES) : (chw ? round16(TW * 4 + 15) : round16(TW * dC * ES + 15));
+        const int orow = chw ? round16(TW * 4 + 15) : round16(TW * dC * ES + 15);
         const uint32_t obase = (uint32_t)(uintptr_t)(J.dst + (int64_t)ty0 * J.dpitch +
                                                      (chw ? (int64_t)tx0 * 4 : (int64_t)tx0 * dC * ES));
         const uint32_t opitch = (uint32_t)J.dpitch, oplane = (uint32_t)J.dplane;
@@ -513,11 +513,11 @@ __device__ __forceinline__ void pipe_consume(Pol &P, PipeShared<TW, TH, NS> &sh,
         }
         for (int ra = UR * warp; ra < (run ? 0 : ny); ra += UR * NWARP) {
             const uint32_t ub = wbuf + (uint32_t)((u & 1) * unit_bytes);
-            // byte offset of (tile row ra + h, plane pl) in the unit stage: dense rows for a TMA
-            // store, else keeping the 16-byte phase of the row in global memory
+            // byte offset of (tile row ra + h, plane pl) in the unit stage, keeping the 16-byte
+            // phase of the row in global memory
             auto row_off = [&](int h, int pl) -> uint32_t {
                 const uint32_t a = obase + (uint32_t)(ra + h) * opitch + (uint32_t)pl * oplane;
-                return ub + (uint32_t)((pl * UR + h) * orow) + (tma_out ? 0u : (a & 15u));
+                return ub + (uint32_t)((pl * UR + h) * orow) + (a & 15u);
             };
             auto orow_of = [&](int h) -> ORow {
                 ORow o;
@@ -643,23 +643,7 @@ __device__ __forceinline__ void pipe_consume(Pol &P, PipeShared<TW, TH, NS> &sh,
             __syncwarp();
 
             // ---- write-out of the unit ----
-            if (tma_out) {
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) {
-                    if (chw) {
-                        for (int pl = 0; pl < 3; ++pl)
-                            tma_store_4d(J.tout, tx0, ty0 + ra, pl, J.zimg, kr_pipe_smem + ub + pl * UR * orow);
-                    } else {
-                        tma_store_3d(J.tout, (tx0 * dC * ES) >> 2, ty0 + ra, J.zimg, kr_pipe_smem + ub);
-                    }
-                    bulk_commit();
-                    // the store of the unit before this one has read the other stage, which the
-                    // next unit writes
-                    bulk_wait_read_1();
-                }
-                __syncwarp();
-            } else {
+            {
                 // every (plane, row) segment of the unit: its 16-byte aligned middle leaves by one
                 // bulk copy from the unit stage (whose rows keep the global rows' 16-byte phase),
                 // the (at most 15 + 15) head and tail bytes by the lanes

@@ -354,17 +354,16 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
     constexpr int NBAND = TH / BH;
     const bool chw = OT::is_f32 && dC == 3 && J.chw;
     const int rph = (fx0 * CIN) & 15;   // phase of every raw-staged row (raw taps)
-    // output rows: dense when the tile leaves through a TMA store (its rows are 16-byte
-    // aligned), else with room for each row's 16-byte phase
-    const bool tma_out = J.tout != nullptr;
-    const int orow = tma_out ? (chw ? TW * 4 : TW * dC * ES) : (chw ? round16(TW * 4 + 15) : round16(TW * dC * ES + 15));
+    // output stage rows (tiles not written straight to global memory), with room for each
+    // row's 16-byte phase
+    const int orow = chw ? round16(TW * 4 + 15) : round16(TW * dC * ES + 15);
     // low address bits of output row 0 of the tile (plane 0): staging rows keep their phase
     const uint32_t obase = (uint32_t)(uintptr_t)(J.dst + (int64_t)ty0 * J.dpitch +
                                                  (chw ? (int64_t)tx0 * 4 : (int64_t)tx0 * dC * ES));
     const uint32_t opitch = (uint32_t)J.dpitch, oplane = (uint32_t)J.dplane;
     // Rows that are whole 16-byte chunks are written straight to global memory by every path
     // (the quad path with 4- or 16-byte stores, the others pixel by pixel): no output stage.
-    const bool direct = tma_out;
+    const bool direct = J.direct != 0;
     int r0 = 0;   // first tile row of the current band
     auto orow_of = [&](int r) -> ORow {
         ORow o;
@@ -734,27 +733,7 @@ __device__ __forceinline__ void process_tile(const Job &J, int tile_x, int tile_
             }
         }
         if (direct) return;   // (written straight to global memory)
-        if (tma_out) fence_proxy_async_smem();
         __syncthreads();
-
-        if (tma_out) {
-            // write-out through TMA stores of the band (rows and chunks past the image's edge
-            // are clipped by the copy engine)
-            if (tid == 0) {
-                if (chw) {
-                    for (int pl = 0; pl < 3; ++pl)
-                        tma_store_4d(J.tout, tx0, ty0 + r0, pl, J.zimg, ostage + pl * BH * orow);
-                } else {
-                    tma_store_3d(J.tout, (tx0 * dC * ES) >> 2, ty0 + r0, J.zimg, ostage);
-                }
-                tma_store_commit_and_wait_read();
-            }
-            // After the last band no closing barrier: this path runs one tile per CTA, the
-            // storing thread waits for the copy engine to finish reading the stage, and a
-            // CTA's shared memory lives until its last thread exits.
-            if (r1 >= ny) return;
-            continue;
-        }
 
         // write-out: 16-byte chunks of every (plane, row) segment of the band spread over the
         // CTA; a second pass, only when some row is not 16-byte aligned at both ends, moves
