@@ -712,7 +712,7 @@ def run_gpu(args):
         if args.extras in ("all", "next-rows") else None
     ragged = ragged_compare(torch, kr, dev, peak) if args.extras == "all" else \
         ragged_compare(torch, kr, dev, peak, autotune=False) if args.extras == "ragged" else None
-    per_config = small_and_strong_downscale(torch, kr, dev, peak) if args.extras == "all" else None
+    per_config = small_and_strong_downscale(torch, kr, dev, peak) if args.extras in ("all", "configs") else None
     serving = serving_compare(torch, kr, dev, seconds=args.serve_seconds, grid=args.serve_grid) \
         if args.extras == "all" else None
     cpu = cpu_baseline_sample() if (rank == 0 and args.extras == "all") else None
@@ -789,9 +789,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--no-extras", action="store_true", help="skip the next rows, the ragged and serving comparisons and the CPU baseline")
-    ap.add_argument("--extras", choices=["all", "next-rows", "ragged", "none"], default="all",
+    ap.add_argument("--extras", choices=["all", "next-rows", "ragged", "configs", "none"], default="all",
                     help="which extra measurements follow the step: all, only the next rows, only the ragged "
-                         "batch (tile configuration 0, no autotuning), or none")
+                         "batch (tile configuration 0, no autotuning), only the 640x480 and 16 x 4K resize "
+                         "configurations, or none")
     ap.add_argument("--next-reps", type=int, default=50, help="timed launches per next row")
     ap.add_argument("--clocks-dir", default=None,
                     help="directory for the raw nvidia-smi clock samples (default: a temporary one)")
