@@ -585,6 +585,40 @@ __device__ __forceinline__ void pipe_consume(Pol &P, PipeShared<TW, TH, NS> &sh,
                             emit<CIN, OUTK>(J, o, c, px_at(ya, xa), px_at(ya, xb), px_at(yb, xa), px_at(yb, xb), qx,
                                             qy, fx, fy);
                         }
+                    } else if (OP != OP_RESIZE && mode == PM_STAGED) {
+                        // staged tile outside the fast forms' range (its box crosses the image's
+                        // edge): the exact weight formula per pixel, every tap read from the
+                        // zero-filled box
+                        const float yc = __fadd_rn((float)y, 0.5f);
+                        const float rx = __fmaf_rn(J.M[1], yc, J.M[2]), ry = __fmaf_rn(J.M[4], yc, J.M[5]);
+#pragma unroll
+                        for (int j = 0; j < TW / 16; ++j) {
+                            const int c = l16 + 16 * j;
+                            if (c >= nx) continue;
+                            float sx, sy;
+                            if (OP == OP_PERSP) {
+                                persp_coord(J.M, tx0 + c, y, sx, sy);   // valid: Z > 0 over the tile
+                            } else {
+                                const float xc = __fadd_rn((float)(tx0 + c), 0.5f);
+                                sx = __fsub_rn(__fmaf_rn(J.M[0], xc, rx), 0.5f);
+                                sy = __fsub_rn(__fmaf_rn(J.M[3], xc, ry), 0.5f);
+                            }
+                            int x0, y0, qx, qy;
+                            warp_weight(sx, x0, qx);
+                            warp_weight(sy, y0, qy);
+                            float fx = 0.f, fy = 0.f;
+                            if (OT::is_f32) {
+                                fx = __fsub_rn(sx, floorf(sx));
+                                fy = __fsub_rn(sy, floorf(sy));
+                            }
+                            const int off = (y0 - fy0) * rstride + 3 * (x0 - fx0) + rph;
+                            const uint8_t *wp = raw + (off & ~3);
+                            const uint32_t sh = (uint32_t)off << 3;
+                            uint32_t p00, p01, p10, p11;
+                            raw_pair(wp, sh, p00, p01);
+                            raw_pair(wp + rstride, sh, p10, p11);
+                            emit<CIN, OUTK, TAPS_RAW>(J, o, c, p00, p01, p10, p11, qx, qy, fx, fy);
+                        }
                     } else {
                         // not staged: per-pixel coordinates with the full rules, taps from global
                         // memory (zero outside the image, or the nearest edge pixel)
