@@ -196,6 +196,29 @@ class Step:
             ("rgb_to_gray", call_gray("rgb_to_gray")),
         ]
 
+    # The step's operations are independent: run_split issues the instruction-bound u8 kinds on
+    # one stream and the f32 kinds and rgb_to_gray, which move the most bytes, on another, so that
+    # their CTAs share the SMs.
+    SPLIT = (("warp_u8", "resize_u8", "warp_gray_u8", "resize_gray_u8"),
+             ("warp_f32", "resize_f32", "resize_norm_f32_chw", "rgb_to_gray"))
+
+    def run_split(self, main, side):
+        """One step on the torch streams `main` and `side` (forked from and joined back into main)."""
+        torch = self.torch
+        if not hasattr(self, "_fork"):
+            self._fork, self._join = torch.cuda.Event(), torch.cuda.Event()
+            self._by_name = dict(self.calls)
+        self._fork.record(main)
+        side.wait_event(self._fork)
+        for names, s in zip(self.SPLIT, (main, side)):
+            h = ctypes.c_void_p(s.cuda_stream)
+            for name in names:
+                st = self._by_name[name](h)
+                if st != 0:
+                    raise RuntimeError(f"{name}: status {st} {self.lib.kr_last_error().decode()}")
+        self._join.record(side)
+        main.wait_event(self._join)
+
     def run(self, stream_handle, events=None):
         for i, (name, c) in enumerate(self.calls):
             if events is not None:
@@ -602,8 +625,9 @@ def run_gpu(args):
     sh = ctypes.c_void_p(stream.cuda_stream)
     ops = op_table()
 
+    side = torch.cuda.Stream() if args.streams == 2 else None
     for _ in range(args.warmup):
-        step.run(sh)
+        step.run(sh) if side is None else step.run_split(stream, side)
     torch.cuda.synchronize()
 
     K = args.steps
@@ -616,7 +640,10 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t_start.record()
         for k in range(K):
-            step.run(sh, events[k])
+            if side is None:
+                step.run(sh, events[k])
+            else:
+                step.run_split(stream, side)
         t_end.record()
         torch.cuda.synchronize()
         if world > 1:
@@ -625,6 +652,12 @@ def run_gpu(args):
     ms_step = ms_total / K
     px_step = n * sum(p for _, p, _ in ops)
     value = world * px_step / (ms_step * 1e-3) / 1e9
+    if side is not None:
+        # per-operation times from the same number of steps run one call after another
+        torch.cuda.synchronize()
+        for k in range(K):
+            step.run(sh, events[k])
+        torch.cuda.synchronize()
 
     # per-operation kernel times (each call is one launch for this batch size)
     per_op = {}
@@ -727,6 +760,7 @@ def run_gpu(args):
             "config": {"workload": WORKLOAD if n == inputs.BENCH_IMAGES else WORKLOAD.replace("32 x", f"{n} x"),
                        "images_per_step": n, "out_px_per_step": px_step,
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "streams": args.streams,
                        "l2": "no flush: 199 MB of distinct source frames per step > 129 MB L2"},
             "roofline": roofline, "per_op": breakdown, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
             "gpu_launches": K * len(ops), "next_rows": widening, "per_config": per_config, "ragged": ragged,
@@ -793,6 +827,10 @@ def main():
                     help="which extra measurements follow the step: all, only the next rows, only the ragged "
                          "batch (tile configuration 0, no autotuning), only the 640x480 and 16 x 4K resize "
                          "configurations, or none")
+    ap.add_argument("--streams", type=int, choices=[1, 2], default=2,
+                    help="streams of the timed step: 1 = the eight calls one after another, 2 = the u8 kinds "
+                         "and the f32 kinds + rgb_to_gray on two streams (per-operation times are always "
+                         "taken one call after another)")
     ap.add_argument("--next-reps", type=int, default=50, help="timed launches per next row")
     ap.add_argument("--clocks-dir", default=None,
                     help="directory for the raw nvidia-smi clock samples (default: a temporary one)")
