@@ -646,18 +646,18 @@ def run_gpu(args):
                 step.run_split(stream, side)
         t_end.record()
         torch.cuda.synchronize()
+        if side is not None:
+            # second timed phase: the same number of steps with the calls one after another, each
+            # call bracketed by CUDA events on its stream (every kernel timed while it runs alone)
+            for k in range(K):
+                step.run(sh, events[k])
+            torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
     ms_total = max_over_ranks(t_start.elapsed_time(t_end), dist if world > 1 else None, dev)
     ms_step = ms_total / K
     px_step = n * sum(p for _, p, _ in ops)
     value = world * px_step / (ms_step * 1e-3) / 1e9
-    if side is not None:
-        # per-operation times from the same number of steps run one call after another
-        torch.cuda.synchronize()
-        for k in range(K):
-            step.run(sh, events[k])
-        torch.cuda.synchronize()
 
     # per-operation kernel times (each call is one launch for this batch size)
     per_op = {}
