@@ -92,3 +92,13 @@ def test_reference_arm_prints_its_line():
     assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] == 3
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_two_stream_step_issues_every_operation_once():
+    """The two-stream step (the default) splits the step's operations between the streams: each
+    of the eight operations exactly once, the u8 kinds on the first stream."""
+    names = [n for n, _, _ in bench.op_table()]
+    first, second = bench.Step.SPLIT
+    assert sorted(first + second) == sorted(names)
+    assert len(set(first + second)) == len(names)
+    assert all(n.endswith("_u8") for n in first)
