@@ -199,25 +199,36 @@ class Step:
     # The step's operations are independent: run_split issues the instruction-bound u8 kinds on
     # one stream and the f32 kinds and rgb_to_gray, which move the most bytes, on another, so that
     # their CTAs share the SMs.
-    SPLIT = (("warp_u8", "resize_u8", "warp_gray_u8", "resize_gray_u8"),
-             ("warp_f32", "resize_f32", "resize_norm_f32_chw", "rgb_to_gray"))
+    SPLITS = {
+        2: (("warp_u8", "resize_u8", "warp_gray_u8", "resize_gray_u8"),
+            ("warp_f32", "resize_f32", "resize_norm_f32_chw", "rgb_to_gray")),
+        3: (("warp_u8", "resize_gray_u8", "rgb_to_gray"), ("warp_gray_u8", "resize_u8"),
+            ("warp_f32", "resize_f32", "resize_norm_f32_chw")),
+        4: (("warp_u8", "resize_u8"), ("warp_gray_u8", "resize_gray_u8"), ("warp_f32", "rgb_to_gray"),
+            ("resize_f32", "resize_norm_f32_chw")),
+    }
+    SPLIT = SPLITS[2]
 
-    def run_split(self, main, side):
-        """One step on the torch streams `main` and `side` (forked from and joined back into main)."""
+    def run_split(self, main, sides):
+        """One step on the torch stream `main` and the streams `sides` (forked from and joined back
+        into main), split as SPLITS[1 + len(sides)]."""
         torch = self.torch
         if not hasattr(self, "_fork"):
-            self._fork, self._join = torch.cuda.Event(), torch.cuda.Event()
+            self._fork = torch.cuda.Event()
+            self._joins = [torch.cuda.Event() for _ in range(3)]
             self._by_name = dict(self.calls)
         self._fork.record(main)
-        side.wait_event(self._fork)
-        for names, s in zip(self.SPLIT, (main, side)):
+        for sd in sides:
+            sd.wait_event(self._fork)
+        for names, s in zip(self.SPLITS[1 + len(sides)], [main] + list(sides)):
             h = ctypes.c_void_p(s.cuda_stream)
             for name in names:
                 st = self._by_name[name](h)
                 if st != 0:
                     raise RuntimeError(f"{name}: status {st} {self.lib.kr_last_error().decode()}")
-        self._join.record(side)
-        main.wait_event(self._join)
+        for sd, ev in zip(sides, self._joins):
+            ev.record(sd)
+            main.wait_event(ev)
 
     def run(self, stream_handle, events=None):
         for i, (name, c) in enumerate(self.calls):
@@ -625,7 +636,7 @@ def run_gpu(args):
     sh = ctypes.c_void_p(stream.cuda_stream)
     ops = op_table()
 
-    side = torch.cuda.Stream() if args.streams == 2 else None
+    side = [torch.cuda.Stream() for _ in range(args.streams - 1)] if args.streams > 1 else None
     for _ in range(args.warmup):
         step.run(sh) if side is None else step.run_split(stream, side)
     torch.cuda.synchronize()
@@ -827,10 +838,10 @@ def main():
                     help="which extra measurements follow the step: all, only the next rows, only the ragged "
                          "batch (tile configuration 0, no autotuning), only the 640x480 and 16 x 4K resize "
                          "configurations, or none")
-    ap.add_argument("--streams", type=int, choices=[1, 2], default=2,
+    ap.add_argument("--streams", type=int, choices=[1, 2, 3, 4], default=2,
                     help="streams of the timed step: 1 = the eight calls one after another, 2 = the u8 kinds "
-                         "and the f32 kinds + rgb_to_gray on two streams (per-operation times are always "
-                         "taken one call after another)")
+                         "and the f32 kinds + rgb_to_gray on two streams, 3-4 = finer splits (Step.SPLITS; "
+                         "per-operation times are always taken one call after another)")
     ap.add_argument("--next-reps", type=int, default=50, help="timed launches per next row")
     ap.add_argument("--clocks-dir", default=None,
                     help="directory for the raw nvidia-smi clock samples (default: a temporary one)")

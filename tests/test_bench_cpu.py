@@ -99,6 +99,8 @@ def test_two_stream_step_issues_every_operation_once():
     of the eight operations exactly once, the u8 kinds on the first stream."""
     names = [n for n, _, _ in bench.op_table()]
     first, second = bench.Step.SPLIT
-    assert sorted(first + second) == sorted(names)
-    assert len(set(first + second)) == len(names)
     assert all(n.endswith("_u8") for n in first)
+    for k, split in bench.Step.SPLITS.items():
+        assert len(split) == k
+        flat = [n for part in split for n in part]
+        assert sorted(flat) == sorted(names) and len(set(flat)) == len(names)
