@@ -5,10 +5,10 @@
 // A CTA holds kPipeConsumers threads (8 warps) that blend tiles and one producer warp that
 // runs ahead of them over the CTA's tiles (claimed from the launch's tile counter):
 //
-//   producer  for tile k: wait until ring slot s = k mod NS is free ("empty" mbarrier, one
-//             arrival per consumer warp), plan the tile into the slot (resize axis tables, or
-//             the warp map at the four tile corners -> source box; fast flag; staging mode),
-//             start the copy of the box into the slot's staging buffer (one TMA tensor copy,
+//   producer  for tile k: plan the tile (resize axis tables, or the warp map at the four tile
+//             corners -> source box; fast flag; staging mode), wait until ring slot
+//             s = k mod NS is free ("empty" mbarrier, one arrival per consumer warp), write the
+//             plan into the slot, start the copy of the box into the slot's staging buffer (one TMA tensor copy,
 //             or one bulk copy per box row with the bytes the copies do not cover written by
 //             the warp: zeros outside the image, the row's last partial 16-byte chunk), then
 //             every lane arrives on the slot's "full" mbarrier (which also completes on the
