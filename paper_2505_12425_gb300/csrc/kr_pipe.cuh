@@ -14,8 +14,9 @@
 //             every lane arrives on the slot's "full" mbarrier (which also completes on the
 //             copies' bytes);
 //   consumers each warp waits on "full" by itself, blends its units of the tile (4 rows for
-//             u8, 2 for f32) from the staged raw rows (or, for a tile that is not staged,
-//             from global memory), writes u8 rows straight to global memory and f32 units
+//             u8, 2 for f32) from the staged raw rows (the quad path, or the exact per-pixel
+//             weights for a tile outside the fast forms' range) or, for a tile that is not
+//             staged, from global memory, writes u8 rows straight to global memory and f32 units
 //             through its own two unit stages in turn (bulk copies of each row's aligned
 //             middle, head and tail bytes by lanes), and releases the slot when it has read it.
 //
